@@ -1,0 +1,1110 @@
+/*
+ * fv_oracle.c -- plain, slow, sequential FP64 CPU oracle of one PISO time step
+ * and one SIMPLE iteration on a face-addressed finite-volume mesh.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this file; it is loaded by the tests, by the package's smoke check
+ * and by the benchmark's CPU-baseline leg.  It shares no code, header, table
+ * or helper with the CUDA path.
+ *
+ * What it follows (the paper, "Complete PISO and SIMPLE solvers on GPUs"):
+ *   Sec. 3    PISO = momentum solve, then a series of pressure solves with
+ *             explicit velocity corrections; SIMPLE = the same steps tuned for
+ *             steady flow; FVM discretisation of the incompressible N-S
+ *             equations; Jacobi-preconditioned CG for the pressure system and
+ *             Jacobi-preconditioned BiCGStab for the non-symmetric momentum
+ *             systems.
+ *   Sec. 3.1  mesh model: N cells, each face shared by two cells or on the
+ *             boundary; A_ij != 0 iff cells i and j share a face or i == j.
+ *   Sec. 4.2  double precision throughout.
+ * The paper gives no discretisation formulas; where it is silent the oracle
+ * takes the textbook collocated finite-volume PISO/SIMPLE (the formulation the
+ * paper says it follows), and every such choice is marked READING below.
+ *
+ * Arithmetic rules: straight sequential loops, sums in face order or cell
+ * order, no blocking, no reordering.  Built with -O2 -ffp-contract=off.
+ *
+ * Storage: vectors of 3 components are stored component-major (SoA):
+ * x[c*n + i].  All arrays inside an omesh / ocase are in the renumbered
+ * ("internal") cell and face order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { P_WALL = 0, P_INLET = 1, P_OUTLET = 2, P_EMPTY = 3 };
+
+typedef struct {
+    int type, start, size;
+} opatch;
+
+typedef struct {
+    int N, F, B, np;
+    int *own;           /* [F+B] */
+    int *nei;           /* [F]   */
+    double *Sf, *Cf;    /* [3*(F+B)] */
+    double *C, *V;      /* [3*N], [N] */
+    double *magSf;      /* [F+B] */
+    double *w;          /* [F] owner interpolation weight */
+    double *delta;      /* [F+B] */
+    double *kv;         /* [3*F] non-orthogonal correction vector */
+    int nonorth;
+    opatch *patch;      /* [np] */
+    int *bpatch;        /* [B] patch of each boundary face */
+    int *cell_new_of_old, *face_new_of_old;
+    signed char *flipped;
+} omesh;
+
+typedef struct {
+    omesh *m;
+    double nu;
+    double *u, *p, *phi;    /* [3N], [N], [F+B] */
+    double *ub, *pb;        /* boundary-face values [3B], [B] */
+} ocase;
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers (sequential)                                         */
+/* ------------------------------------------------------------------------ */
+
+static double dot_n(int n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static double norm2_n(int n, const double *a) { return sqrt(dot_n(n, a, a)); }
+
+static void *xcalloc(size_t n, size_t sz)
+{
+    void *p = calloc(n ? n : 1, sz);
+    if (!p) abort();
+    return p;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse Cuthill-McKee renumbering.                                         */
+/* READING (the paper only asks for a GPU-friendly data layout, Sec. 3.1):   */
+/*  - graph = cells joined by internal faces;                                */
+/*  - start: unvisited cell of minimum degree, ties -> lowest current index; */
+/*  - BFS; the unvisited neighbours of each dequeued cell are appended in    */
+/*    ascending (degree, index) order;                                       */
+/*  - further components restart the same way; the whole order is reversed; */
+/*  - no pseudo-peripheral search.                                           */
+/* ------------------------------------------------------------------------ */
+
+static const int *g_deg_for_sort;
+static int cmp_deg_idx(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    if (g_deg_for_sort[x] != g_deg_for_sort[y]) return g_deg_for_sort[x] < g_deg_for_sort[y] ? -1 : 1;
+    return (x > y) - (x < y);
+}
+
+static void rcm_order(int N, int F, const int *own, const int *nei, int *new_of_old)
+{
+    int *deg = xcalloc(N, sizeof(int));
+    for (int f = 0; f < F; ++f) { deg[own[f]]++; deg[nei[f]]++; }
+    int *start = xcalloc(N + 1, sizeof(int));
+    for (int i = 0; i < N; ++i) start[i + 1] = start[i] + deg[i];
+    int *fill = xcalloc(N, sizeof(int));
+    int *adj = xcalloc(start[N], sizeof(int));
+    for (int f = 0; f < F; ++f) {
+        adj[start[own[f]] + fill[own[f]]++] = nei[f];
+        adj[start[nei[f]] + fill[nei[f]]++] = own[f];
+    }
+    g_deg_for_sort = deg;
+    for (int i = 0; i < N; ++i) qsort(adj + start[i], deg[i], sizeof(int), cmp_deg_idx);
+
+    char *visited = xcalloc(N, 1);
+    int *order = xcalloc(N, sizeof(int));
+    int head = 0, tail = 0;
+    while (tail < N) {
+        int s = -1;
+        for (int i = 0; i < N; ++i)
+            if (!visited[i] && (s < 0 || deg[i] < deg[s])) s = i;
+        visited[s] = 1;
+        order[tail++] = s;
+        while (head < tail) {
+            int v = order[head++];
+            for (int k = start[v]; k < start[v + 1]; ++k) {
+                int u = adj[k];
+                if (!visited[u]) { visited[u] = 1; order[tail++] = u; }
+            }
+        }
+    }
+    for (int pos = 0; pos < N; ++pos) new_of_old[order[N - 1 - pos]] = pos;
+    free(deg); free(start); free(fill); free(adj); free(visited); free(order);
+}
+
+/* face sort keys */
+typedef struct { long long k1, k2, k3; int idx; } fkey;
+static int cmp_fkey(const void *a, const void *b)
+{
+    const fkey *x = a, *y = b;
+    if (x->k1 != y->k1) return x->k1 < y->k1 ? -1 : 1;
+    if (x->k2 != y->k2) return x->k2 < y->k2 ? -1 : 1;
+    if (x->k3 != y->k3) return x->k3 < y->k3 ? -1 : 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh construction: renumbering, face orientation/order, geometry.          */
+/* ------------------------------------------------------------------------ */
+
+omesh *orc_mesh_new(int N, int F, int B, const int *own_in, const int *nei_in,
+                    const double *Sf_in, const double *Cf_in, const double *C_in,
+                    const double *V_in, int np, const int *ptype, const int *pstart,
+                    const int *psize, int renumber)
+{
+    omesh *m = xcalloc(1, sizeof(omesh));
+    int M = F + B;
+    m->N = N; m->F = F; m->B = B; m->np = np;
+    m->cell_new_of_old = xcalloc(N, sizeof(int));
+    m->face_new_of_old = xcalloc(M, sizeof(int));
+    m->flipped = xcalloc(M, 1);
+    if (renumber) rcm_order(N, F, own_in, nei_in, m->cell_new_of_old);
+    else for (int i = 0; i < N; ++i) m->cell_new_of_old[i] = i;
+    const int *no = m->cell_new_of_old;
+
+    /* internal faces: orient owner < neighbour, sort by (owner, neighbour) */
+    fkey *keys = xcalloc(M, sizeof(fkey));
+    for (int f = 0; f < F; ++f) {
+        int a = no[own_in[f]], b = no[nei_in[f]];
+        keys[f].k1 = a < b ? a : b;
+        keys[f].k2 = a < b ? b : a;
+        keys[f].k3 = f;
+        keys[f].idx = f;
+        m->flipped[f] = a > b;
+    }
+    qsort(keys, F, sizeof(fkey), cmp_fkey);
+    for (int pos = 0; pos < F; ++pos) m->face_new_of_old[keys[pos].idx] = pos;
+    /* boundary faces: sort by (patch, new owner, original index) */
+    m->patch = xcalloc(np, sizeof(opatch));
+    for (int b = 0; b < B; ++b) {
+        int pat = -1;
+        for (int q = 0; q < np; ++q)
+            if (b >= pstart[q] && b < pstart[q] + psize[q]) pat = q;
+        keys[b].k1 = pat;
+        keys[b].k2 = no[own_in[F + b]];
+        keys[b].k3 = b;
+        keys[b].idx = b;
+    }
+    qsort(keys, B, sizeof(fkey), cmp_fkey);
+    for (int pos = 0; pos < B; ++pos) m->face_new_of_old[F + keys[pos].idx] = F + pos;
+    free(keys);
+    for (int q = 0; q < np; ++q) {
+        m->patch[q].type = ptype[q];
+        m->patch[q].start = pstart[q];   /* the sort keeps every patch in place */
+        m->patch[q].size = psize[q];
+    }
+    m->bpatch = xcalloc(B, sizeof(int));
+    for (int q = 0; q < np; ++q)
+        for (int j = 0; j < psize[q]; ++j) m->bpatch[pstart[q] + j] = q;
+
+    /* renumbered arrays */
+    m->own = xcalloc(M, sizeof(int));
+    m->nei = xcalloc(F, sizeof(int));
+    m->Sf = xcalloc(3 * (size_t)M, sizeof(double));
+    m->Cf = xcalloc(3 * (size_t)M, sizeof(double));
+    m->C = xcalloc(3 * (size_t)N, sizeof(double));
+    m->V = xcalloc(N, sizeof(double));
+    for (int f = 0; f < M; ++f) {
+        int fn = m->face_new_of_old[f];
+        double sgn = m->flipped[f] ? -1.0 : 1.0;
+        if (f < F) {
+            int a = no[own_in[f]], b = no[nei_in[f]];
+            m->own[fn] = a < b ? a : b;
+            m->nei[fn] = a < b ? b : a;
+        } else {
+            m->own[fn] = no[own_in[f]];
+        }
+        for (int c = 0; c < 3; ++c) {
+            m->Sf[c * M + fn] = sgn * Sf_in[c * M + f];
+            m->Cf[c * M + fn] = Cf_in[c * M + f];
+        }
+    }
+    for (int i = 0; i < N; ++i) {
+        for (int c = 0; c < 3; ++c) m->C[c * N + no[i]] = C_in[c * N + i];
+        m->V[no[i]] = V_in[i];
+    }
+
+    /* geometry.  READINGS (the paper defers the discretisation to the
+     * textbook finite-volume method):
+     *  n = S/|S|, d = C_N - C_P;
+     *  w = n.(C_N - Cf) / (n.(C_N - Cf) + n.(Cf - C_P))   (face value
+     *      x_f = w x_P + (1-w) x_N);
+     *  delta = 1 / max(n.d, 0.05 |d|);  k = n - delta d  (over-relaxed split
+     *      S = |S| delta d + |S| k);
+     *  boundary: d = Cf - C_P, delta = 1/max(n.d, 0.05|d|), no k. */
+    m->magSf = xcalloc(M, sizeof(double));
+    m->w = xcalloc(F ? F : 1, sizeof(double));
+    m->delta = xcalloc(M, sizeof(double));
+    m->kv = xcalloc(3 * (size_t)(F ? F : 1), sizeof(double));
+    m->nonorth = 0;
+    for (int f = 0; f < M; ++f) {
+        double S[3], n[3], d[3], cf[3], cp[3];
+        for (int c = 0; c < 3; ++c) {
+            S[c] = m->Sf[c * M + f];
+            cf[c] = m->Cf[c * M + f];
+            cp[c] = m->C[c * N + m->own[f]];
+        }
+        double mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+        m->magSf[f] = mag;
+        for (int c = 0; c < 3; ++c) n[c] = S[c] / mag;
+        if (f < F) {
+            double cn[3];
+            for (int c = 0; c < 3; ++c) cn[c] = m->C[c * N + m->nei[f]];
+            double a1 = 0.0, a2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                a1 += n[c] * (cn[c] - cf[c]);
+                a2 += n[c] * (cf[c] - cp[c]);
+            }
+            m->w[f] = a1 / (a1 + a2);
+            for (int c = 0; c < 3; ++c) d[c] = cn[c] - cp[c];
+        } else {
+            for (int c = 0; c < 3; ++c) d[c] = cf[c] - cp[c];
+        }
+        double nd = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+        double dm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double den = nd > 0.05 * dm ? nd : 0.05 * dm;
+        m->delta[f] = 1.0 / den;
+        if (f < F) {
+            double kk = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double k = n[c] - m->delta[f] * d[c];
+                m->kv[c * F + f] = k;
+                kk += k * k;
+            }
+            /* READING: the explicit non-orthogonal terms are switched on for a
+             * mesh iff some internal face has |k| > 1e-8 (|k| is
+             * dimensionless); on orthogonal hexahedra |k| is rounding noise. */
+            if (sqrt(kk) > 1e-8) m->nonorth = 1;
+        }
+    }
+    return m;
+}
+
+void orc_mesh_free(omesh *m)
+{
+    if (!m) return;
+    free(m->own); free(m->nei); free(m->Sf); free(m->Cf); free(m->C); free(m->V);
+    free(m->magSf); free(m->w); free(m->delta); free(m->kv); free(m->patch);
+    free(m->bpatch); free(m->cell_new_of_old); free(m->face_new_of_old); free(m->flipped);
+    free(m);
+}
+
+void orc_mesh_orders(const omesh *m, int *cell_new_of_old, int *face_new_of_old, signed char *flipped)
+{
+    memcpy(cell_new_of_old, m->cell_new_of_old, sizeof(int) * m->N);
+    memcpy(face_new_of_old, m->face_new_of_old, sizeof(int) * (m->F + m->B));
+    memcpy(flipped, m->flipped, m->F + m->B);
+}
+
+void orc_mesh_addressing(const omesh *m, int *own, int *nei)
+{
+    memcpy(own, m->own, sizeof(int) * (m->F + m->B));
+    memcpy(nei, m->nei, sizeof(int) * m->F);
+}
+
+void orc_mesh_geometry(const omesh *m, double *magSf, double *w, double *delta, double *kv,
+                       double *Sf, double *V)
+{
+    int M = m->F + m->B;
+    memcpy(magSf, m->magSf, sizeof(double) * M);
+    memcpy(w, m->w, sizeof(double) * m->F);
+    memcpy(delta, m->delta, sizeof(double) * M);
+    memcpy(kv, m->kv, sizeof(double) * 3 * m->F);
+    memcpy(Sf, m->Sf, sizeof(double) * 3 * M);
+    memcpy(V, m->V, sizeof(double) * m->N);
+}
+
+int orc_mesh_nonorth(const omesh *m) { return m->nonorth; }
+
+/* ------------------------------------------------------------------------ */
+/* LDU matrix-vector product (the paper's SMVP, Sec. 4.3.2):                  */
+/* row P: diag_P x_P + sum_{f: own=P} upper_f x_nei + sum_{f: nei=P} lower_f x_own */
+/* ------------------------------------------------------------------------ */
+
+static void ldu_matvec(int N, int F, const int *own, const int *nei, const double *diag,
+                       const double *upper, const double *lower, const double *x, double *y)
+{
+    for (int i = 0; i < N; ++i) y[i] = diag[i] * x[i];
+    for (int f = 0; f < F; ++f) {
+        y[own[f]] += upper[f] * x[nei[f]];
+        y[nei[f]] += lower[f] * x[own[f]];
+    }
+}
+
+void orc_ldu_matvec(int N, int F, const int *own, const int *nei, const double *diag,
+                    const double *upper, const double *lower, const double *x, double *y)
+{
+    ldu_matvec(N, F, own, nei, diag, upper, lower, x, y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Jacobi-preconditioned CG (paper Sec. 3 and Sec. 4.3.2: SMVP, daxpy, dot,  */
+/* reduction and the diagonal preconditioner).                               */
+/* READING: warm start from x; stop when ||r||_2 <= max(tol ||b||_2,          */
+/* reltol ||r_0||_2), r the recursively updated residual, tested before the  */
+/* first iteration and after every r update; ||b|| = 0 returns x = 0.        */
+/* Returns the iteration count (number of SMVPs); -1 if not converged,       */
+/* -2 on breakdown (non-positive or non-finite curvature).                   */
+/* ------------------------------------------------------------------------ */
+
+int orc_pcg(int N, int F, const int *own, const int *nei, const double *diag,
+            const double *upper, const double *b, double *x, double tol, double reltol,
+            int maxit, double *res0_out, double *res_out, int *iters_out)
+{
+    double *r = xcalloc(N, sizeof(double)), *z = xcalloc(N, sizeof(double));
+    double *p = xcalloc(N, sizeof(double)), *q = xcalloc(N, sizeof(double));
+    int status = 0, it = 0;
+    double nb = norm2_n(N, b);
+    if (nb == 0.0) {
+        for (int i = 0; i < N; ++i) x[i] = 0.0;
+        *res0_out = 0.0; *res_out = 0.0; *iters_out = 0;
+        free(r); free(z); free(p); free(q);
+        return 0;
+    }
+    ldu_matvec(N, F, own, nei, diag, upper, upper, x, q);
+    for (int i = 0; i < N; ++i) r[i] = b[i] - q[i];
+    double nr = norm2_n(N, r);
+    double thresh = tol * nb;
+    if (reltol * nr > thresh) thresh = reltol * nr;
+    *res0_out = nr / nb;
+    if (nr <= thresh) goto done;
+    for (int i = 0; i < N; ++i) z[i] = r[i] / diag[i];
+    for (int i = 0; i < N; ++i) p[i] = z[i];
+    double rho = dot_n(N, r, z);
+    for (it = 1; it <= maxit; ++it) {
+        ldu_matvec(N, F, own, nei, diag, upper, upper, p, q);
+        double pq = dot_n(N, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = -2; break; }
+        double alpha = rho / pq;
+        for (int i = 0; i < N; ++i) x[i] += alpha * p[i];
+        for (int i = 0; i < N; ++i) r[i] -= alpha * q[i];
+        nr = norm2_n(N, r);
+        if (!isfinite(nr)) { status = -2; break; }
+        if (nr <= thresh) break;
+        if (it == maxit) { status = -1; break; }
+        for (int i = 0; i < N; ++i) z[i] = r[i] / diag[i];
+        double rho_new = dot_n(N, r, z);
+        double beta = rho_new / rho;
+        rho = rho_new;
+        for (int i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (it > maxit) status = -1;
+done:
+    *res_out = nr / nb;
+    *iters_out = it > maxit ? maxit : it;
+    free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Jacobi (right) preconditioned BiCGStab of van der Vorst for the momentum  */
+/* systems (paper Sec. 3).  Shadow residual r^ = r_0.                         */
+/* READING: same stopping rule as CG, tested before the first iteration and  */
+/* after each full iteration (no half-step exit); ||b|| = 0 returns x = 0.    */
+/* ------------------------------------------------------------------------ */
+
+int orc_bicgstab(int N, int F, const int *own, const int *nei, const double *diag,
+                 const double *upper, const double *lower, const double *b, double *x,
+                 double tol, double reltol, int maxit, double *res0_out, double *res_out,
+                 int *iters_out)
+{
+    double *r = xcalloc(N, sizeof(double)), *rh = xcalloc(N, sizeof(double));
+    double *p = xcalloc(N, sizeof(double)), *v = xcalloc(N, sizeof(double));
+    double *y = xcalloc(N, sizeof(double)), *s = xcalloc(N, sizeof(double));
+    double *z = xcalloc(N, sizeof(double)), *t = xcalloc(N, sizeof(double));
+    int status = 0, it = 0;
+    double nb = norm2_n(N, b), nr = 0.0;
+    if (nb == 0.0) {
+        for (int i = 0; i < N; ++i) x[i] = 0.0;
+        *res0_out = 0.0; *res_out = 0.0; *iters_out = 0;
+        goto out;
+    }
+    ldu_matvec(N, F, own, nei, diag, upper, lower, x, t);
+    for (int i = 0; i < N; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; }
+    nr = norm2_n(N, r);
+    double thresh = tol * nb;
+    if (reltol * nr > thresh) thresh = reltol * nr;
+    *res0_out = nr / nb;
+    if (nr <= thresh) goto done;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    for (it = 1; it <= maxit; ++it) {
+        double rho = dot_n(N, rh, r);
+        if (it == 1) {
+            for (int i = 0; i < N; ++i) p[i] = r[i];
+        } else {
+            double beta = (rho / rho_old) * (alpha / omega);
+            for (int i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        }
+        for (int i = 0; i < N; ++i) y[i] = p[i] / diag[i];
+        ldu_matvec(N, F, own, nei, diag, upper, lower, y, v);
+        double rv = dot_n(N, rh, v);
+        if (rv == 0.0 || !isfinite(rv)) { status = -2; break; }
+        alpha = rho / rv;
+        for (int i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
+        for (int i = 0; i < N; ++i) z[i] = s[i] / diag[i];
+        ldu_matvec(N, F, own, nei, diag, upper, lower, z, t);
+        double ts = dot_n(N, t, s), tt = dot_n(N, t, t);
+        omega = tt > 0.0 ? ts / tt : 0.0;
+        for (int i = 0; i < N; ++i) x[i] += alpha * y[i] + omega * z[i];
+        for (int i = 0; i < N; ++i) r[i] = s[i] - omega * t[i];
+        nr = norm2_n(N, r);
+        if (!isfinite(nr)) { status = -2; break; }
+        if (nr <= thresh) break;
+        if (it == maxit) { status = -1; break; }
+        if (omega == 0.0) { status = -2; break; }
+        rho_old = rho;
+    }
+    if (it > maxit) status = -1;
+done:
+    *res_out = nr / nb;
+    *iters_out = it > maxit ? maxit : it;
+out:
+    free(r); free(rh); free(p); free(v); free(y); free(s); free(z); free(t);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense Gaussian elimination with partial pivoting (pin for the Krylov      */
+/* solvers on tiny meshes).  A is n x n row-major, overwritten; b := A^-1 b. */
+/* ------------------------------------------------------------------------ */
+
+int orc_dense_solve(int n, double *A, double *b)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(A[(size_t)i * n + k]) > fabs(A[(size_t)piv * n + k])) piv = i;
+        if (A[(size_t)piv * n + k] == 0.0) return -1;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(size_t)k * n + j];
+                A[(size_t)k * n + j] = A[(size_t)piv * n + j];
+                A[(size_t)piv * n + j] = t;
+            }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            for (int j = k; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = b[k];
+        for (int j = k + 1; j < n; ++j) s -= A[(size_t)k * n + j] * b[j];
+        b[k] = s / A[(size_t)k * n + k];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Case (fields + boundary values)                                            */
+/* ------------------------------------------------------------------------ */
+
+ocase *orc_case_new(omesh *m, double nu)
+{
+    ocase *cs = xcalloc(1, sizeof(ocase));
+    cs->m = m;
+    cs->nu = nu;
+    cs->u = xcalloc(3 * (size_t)m->N, sizeof(double));
+    cs->p = xcalloc(m->N, sizeof(double));
+    cs->phi = xcalloc(m->F + m->B, sizeof(double));
+    cs->ub = xcalloc(3 * (size_t)(m->B ? m->B : 1), sizeof(double));
+    cs->pb = xcalloc(m->B ? m->B : 1, sizeof(double));
+    return cs;
+}
+
+void orc_case_free(ocase *cs)
+{
+    if (!cs) return;
+    free(cs->u); free(cs->p); free(cs->phi); free(cs->ub); free(cs->pb);
+    free(cs);
+}
+
+/* fields in the caller's (original) order when original_order != 0:
+ * u [3][N], p [N], phi [F+B] with the caller's face orientation. */
+void orc_case_set_fields(ocase *cs, const double *u, const double *p, const double *phi,
+                         int original_order)
+{
+    const omesh *m = cs->m;
+    int N = m->N, M = m->F + m->B;
+    for (int i = 0; i < N; ++i) {
+        int j = original_order ? m->cell_new_of_old[i] : i;
+        for (int c = 0; c < 3; ++c) cs->u[c * N + j] = u[c * N + i];
+        cs->p[j] = p[i];
+    }
+    for (int f = 0; f < M; ++f) {
+        int g = original_order ? m->face_new_of_old[f] : f;
+        double s = (original_order && m->flipped[f]) ? -1.0 : 1.0;
+        cs->phi[g] = s * phi[f];
+    }
+}
+
+void orc_case_get_fields(const ocase *cs, double *u, double *p, double *phi, int original_order)
+{
+    const omesh *m = cs->m;
+    int N = m->N, M = m->F + m->B;
+    for (int i = 0; i < N; ++i) {
+        int j = original_order ? m->cell_new_of_old[i] : i;
+        for (int c = 0; c < 3; ++c) u[c * N + i] = cs->u[c * N + j];
+        p[i] = cs->p[j];
+    }
+    for (int f = 0; f < M; ++f) {
+        int g = original_order ? m->face_new_of_old[f] : f;
+        double s = (original_order && m->flipped[f]) ? -1.0 : 1.0;
+        phi[f] = s * cs->phi[g];
+    }
+}
+
+/* Uniform value on one patch (time-dependent boundary conditions, Sec. 1/6). */
+void orc_patch_set_value(ocase *cs, int q, const double *u3, double p)
+{
+    const omesh *m = cs->m;
+    for (int j = 0; j < m->patch[q].size; ++j) {
+        int b = m->patch[q].start + j;
+        for (int c = 0; c < 3; ++c) cs->ub[c * m->B + b] = u3[c];
+        cs->pb[b] = p;
+    }
+}
+
+/* Per-face values on one patch, given in the caller's face order within the
+ * patch: u [3][size], p [size] (p may be NULL). */
+void orc_patch_set_face_values(ocase *cs, int q, const double *u, const double *p)
+{
+    const omesh *m = cs->m;
+    int size = m->patch[q].size;
+    for (int j = 0; j < size; ++j) {
+        int b = m->face_new_of_old[m->F + m->patch[q].start + j] - m->F;
+        for (int c = 0; c < 3; ++c) cs->ub[c * m->B + b] = u[c * size + j];
+        if (p) cs->pb[b] = p[j];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Finite-volume operators (paper Sec. 4.3.3: gradient, divergence,           */
+/* Laplacian).                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Gauss gradient: grad x_P = (1/V_P) [ sum_int (+-S_f) x_f + sum_bnd S_b x_b ],
+ * x_f = w x_P + (1-w) x_N; empty faces are skipped. */
+static void gauss_grad(const omesh *m, const double *x, const double *xb, double *g)
+{
+    int N = m->N, F = m->F, B = m->B, M = F + B;
+    for (int i = 0; i < 3 * N; ++i) g[i] = 0.0;
+    for (int f = 0; f < F; ++f) {
+        int P = m->own[f], Q = m->nei[f];
+        double xf = m->w[f] * x[P] + (1.0 - m->w[f]) * x[Q];
+        for (int c = 0; c < 3; ++c) {
+            g[c * N + P] += m->Sf[c * M + f] * xf;
+            g[c * N + Q] -= m->Sf[c * M + f] * xf;
+        }
+    }
+    for (int b = 0; b < B; ++b) {
+        int fb = F + b;
+        if (m->patch[m->bpatch[b]].type == P_EMPTY) continue;
+        int P = m->own[fb];
+        for (int c = 0; c < 3; ++c) g[c * N + P] += m->Sf[c * M + fb] * xb[b];
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int i = 0; i < N; ++i) g[c * N + i] /= m->V[i];
+}
+
+/* boundary values of p: fixed on outlets, zero-gradient elsewhere */
+static void p_boundary(const ocase *cs, const double *p, double *xb)
+{
+    const omesh *m = cs->m;
+    for (int b = 0; b < m->B; ++b) {
+        int t = m->patch[m->bpatch[b]].type;
+        xb[b] = (t == P_OUTLET) ? cs->pb[b] : p[m->own[m->F + b]];
+    }
+}
+
+/* boundary values of velocity component c: fixed on walls and inlets,
+ * zero-gradient on outlets */
+static void u_boundary(const ocase *cs, int c, const double *uc, double *xb)
+{
+    const omesh *m = cs->m;
+    for (int b = 0; b < m->B; ++b) {
+        int t = m->patch[m->bpatch[b]].type;
+        xb[b] = (t == P_WALL || t == P_INLET) ? cs->ub[c * m->B + b] : uc[m->own[m->F + b]];
+    }
+}
+
+static void grad_p(const ocase *cs, const double *p, double *g)
+{
+    double *xb = xcalloc(cs->m->B, sizeof(double));
+    p_boundary(cs, p, xb);
+    gauss_grad(cs->m, p, xb, g);
+    free(xb);
+}
+
+/* gradU [9N]: component-major, gradU[(3c + d) N + i] = d u_c / d x_d */
+static void grad_u(const ocase *cs, double *gU)
+{
+    const omesh *m = cs->m;
+    int N = m->N;
+    double *xb = xcalloc(m->B, sizeof(double));
+    for (int c = 0; c < 3; ++c) {
+        u_boundary(cs, c, cs->u + (size_t)c * N, xb);
+        gauss_grad(m, cs->u + (size_t)c * N, xb, gU + (size_t)3 * c * N);
+    }
+    free(xb);
+}
+
+void orc_case_grad_p(const ocase *cs, double *g) { grad_p(cs, cs->p, g); }
+
+/* ------------------------------------------------------------------------ */
+/* Momentum matrix M (LDU) and source (paper Sec. 3: the momentum equation   */
+/* solved first in PISO/SIMPLE).  READINGS:                                   */
+/*  ddt (PISO): Euler implicit, diag += V/dt, src += V/dt u^n;                */
+/*  convection: central ("linear") face value, flux F = phi_f out of P:       */
+/*     diag_P += F w, upper += F (1-w); diag_N -= F (1-w), lower -= F w;      */
+/*  diffusion D = nu |S| delta: diag_P += D, diag_N += D, upper -= D,         */
+/*     lower -= D; explicit non-orthogonal term nu |S| k.(grad u)_f added to  */
+/*     src_P and subtracted from src_N (gradient of the current u);           */
+/*  fixed-U boundary: src += (nu |S| delta_b - F_b) u_b, diag += nu|S|delta_b;*/
+/*  outlet (zero-gradient U): diag += F_b;                                     */
+/*  SIMPLE: no ddt; implicit relaxation diag' = diag/alpha,                   */
+/*     src += (diag' - diag) u_prev.                                           */
+/* The pressure gradient is NOT part of src.                                   */
+/* ------------------------------------------------------------------------ */
+
+static void assemble_momentum(const ocase *cs, int transient, double dt, double alpha_u,
+                              const double *gU, double *diag, double *upper, double *lower,
+                              double *src)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F, B = m->B, M = F + B;
+    double nu = cs->nu;
+    for (int i = 0; i < N; ++i) diag[i] = 0.0;
+    for (int i = 0; i < 3 * N; ++i) src[i] = 0.0;
+    for (int f = 0; f < F; ++f) { upper[f] = 0.0; lower[f] = 0.0; }
+    if (transient) {
+        for (int i = 0; i < N; ++i) {
+            double vdt = m->V[i] / dt;
+            diag[i] += vdt;
+            for (int c = 0; c < 3; ++c) src[c * N + i] += vdt * cs->u[c * N + i];
+        }
+    }
+    for (int f = 0; f < F; ++f) {
+        int P = m->own[f], Q = m->nei[f];
+        double Fl = cs->phi[f], w = m->w[f];
+        diag[P] += Fl * w;
+        upper[f] += Fl * (1.0 - w);
+        diag[Q] -= Fl * (1.0 - w);
+        lower[f] -= Fl * w;
+        double D = nu * m->magSf[f] * m->delta[f];
+        diag[P] += D;
+        diag[Q] += D;
+        upper[f] -= D;
+        lower[f] -= D;
+        if (m->nonorth) {
+            for (int c = 0; c < 3; ++c) {
+                double kg = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double gf = w * gU[(3 * c + d) * N + P] + (1.0 - w) * gU[(3 * c + d) * N + Q];
+                    kg += m->kv[d * F + f] * gf;
+                }
+                double t = nu * m->magSf[f] * kg;
+                src[c * N + P] += t;
+                src[c * N + Q] -= t;
+            }
+        }
+    }
+    for (int b = 0; b < B; ++b) {
+        int fb = F + b, P = m->own[fb];
+        int t = m->patch[m->bpatch[b]].type;
+        if (t == P_EMPTY) continue;
+        if (t == P_WALL || t == P_INLET) {
+            double D = nu * m->magSf[fb] * m->delta[fb];
+            double Fb = cs->phi[fb];
+            diag[P] += D;
+            for (int c = 0; c < 3; ++c) {
+                double ubc = cs->ub[c * B + b];
+                src[c * N + P] += D * ubc - Fb * ubc;
+            }
+        } else if (t == P_OUTLET) {
+            diag[P] += cs->phi[fb];
+        }
+    }
+    (void)M;
+    if (!transient) {
+        for (int i = 0; i < N; ++i) {
+            double d0 = diag[i], d1 = d0 / alpha_u;
+            diag[i] = d1;
+            for (int c = 0; c < 3; ++c) src[c * N + i] += (d1 - d0) * cs->u[c * N + i];
+        }
+    }
+}
+
+void orc_case_momentum_system(const ocase *cs, int transient, double dt, double alpha_u,
+                              double *diag, double *upper, double *lower, double *src)
+{
+    const omesh *m = cs->m;
+    double *gU = m->nonorth ? xcalloc(9 * (size_t)m->N, sizeof(double)) : NULL;
+    if (gU) grad_u(cs, gU);
+    assemble_momentum(cs, transient, dt, alpha_u, gU, diag, upper, lower, src);
+    free(gU);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pressure step pieces (paper Sec. 3: pressure solve + explicit velocity    */
+/* correction).  READINGS:                                                    */
+/*  A_P = diag of M; H_P = src_P - sum offdiag u_nbr; HbyA = H/A;             */
+/*  rAU = V/A; phi*_f = (interp HbyA)_f . S_f (no time-derivative flux term); */
+/*  boundary phi*: fixed-U -> u_b.S_b, outlet -> HbyA_P.S_b;                  */
+/*  pressure matrix = negated Laplacian of rAU (SPD): a_f = rAU_f |S| delta,  */
+/*  rAU_f = w rAU_P + (1-w) rAU_N, diag += a_f both sides, upper = -a_f;      */
+/*  fixed-p (outlet) face: a_b = rAU_P |S| delta_b, diag += a_b, b += a_b p_b;*/
+/*  b_P = -sum_out phi*  + sum_out rAU_f |S| k.(grad p)_f (lagged gradient);  */
+/*  reference cell r (closed domains): b_r += diag_r p_ref, diag_r *= 2;      */
+/*  flux: phi_f = phi*_f - a_f (p_N - p_P) - rAU_f |S| k.(grad p)_f,          */
+/*        outlet phi_b = phi*_b - a_b (p_b - p_P);                            */
+/*  velocity: u = HbyA - rAU grad p.                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double *HbyA, *rAU, *phis, *af, *nof, *pdiag, *pup, *pb;
+} pwork;
+
+static void pwork_alloc(pwork *w, const omesh *m)
+{
+    int N = m->N, M = m->F + m->B;
+    w->HbyA = xcalloc(3 * (size_t)N, sizeof(double));
+    w->rAU = xcalloc(N, sizeof(double));
+    w->phis = xcalloc(M, sizeof(double));
+    w->af = xcalloc(M, sizeof(double));
+    w->nof = xcalloc(m->F ? m->F : 1, sizeof(double));
+    w->pdiag = xcalloc(N, sizeof(double));
+    w->pup = xcalloc(m->F ? m->F : 1, sizeof(double));
+    w->pb = xcalloc(N, sizeof(double));
+}
+
+static void pwork_free(pwork *w)
+{
+    free(w->HbyA); free(w->rAU); free(w->phis); free(w->af); free(w->nof);
+    free(w->pdiag); free(w->pup); free(w->pb);
+}
+
+static void compute_HbyA(const ocase *cs, const double *mdiag, const double *upper,
+                         const double *lower, const double *src, pwork *w)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F;
+    for (int c = 0; c < 3; ++c) {
+        double *H = w->HbyA + (size_t)c * N;
+        const double *uc = cs->u + (size_t)c * N;
+        for (int i = 0; i < N; ++i) H[i] = src[c * N + i];
+        for (int f = 0; f < F; ++f) {
+            H[m->own[f]] -= upper[f] * uc[m->nei[f]];
+            H[m->nei[f]] -= lower[f] * uc[m->own[f]];
+        }
+        for (int i = 0; i < N; ++i) H[i] /= mdiag[i];
+    }
+    for (int i = 0; i < N; ++i) w->rAU[i] = m->V[i] / mdiag[i];
+}
+
+static void assemble_pressure(const ocase *cs, const double *gradp, int ref_cell, double p_ref,
+                              pwork *w)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F, B = m->B, M = F + B;
+    for (int i = 0; i < N; ++i) { w->pdiag[i] = 0.0; w->pb[i] = 0.0; }
+    for (int f = 0; f < M; ++f) { w->phis[f] = 0.0; w->af[f] = 0.0; }
+    for (int f = 0; f < F; ++f) {
+        int P = m->own[f], Q = m->nei[f];
+        double wf = m->w[f];
+        double ph = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double hf = wf * w->HbyA[c * N + P] + (1.0 - wf) * w->HbyA[c * N + Q];
+            ph += hf * m->Sf[c * M + f];
+        }
+        w->phis[f] = ph;
+        double rf = wf * w->rAU[P] + (1.0 - wf) * w->rAU[Q];
+        double a = rf * m->magSf[f] * m->delta[f];
+        w->af[f] = a;
+        w->pdiag[P] += a;
+        w->pdiag[Q] += a;
+        w->pup[f] = -a;
+        w->pb[P] -= ph;
+        w->pb[Q] += ph;
+        w->nof[f] = 0.0;
+        if (m->nonorth) {
+            double kg = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double gf = wf * gradp[d * N + P] + (1.0 - wf) * gradp[d * N + Q];
+                kg += m->kv[d * F + f] * gf;
+            }
+            double nf = rf * m->magSf[f] * kg;
+            w->nof[f] = nf;
+            w->pb[P] += nf;
+            w->pb[Q] -= nf;
+        }
+    }
+    for (int b = 0; b < B; ++b) {
+        int fb = F + b, P = m->own[fb];
+        int t = m->patch[m->bpatch[b]].type;
+        if (t == P_EMPTY) continue;
+        double ph = 0.0;
+        if (t == P_WALL || t == P_INLET) {
+            for (int c = 0; c < 3; ++c) ph += cs->ub[c * B + b] * m->Sf[c * M + fb];
+        } else {
+            for (int c = 0; c < 3; ++c) ph += w->HbyA[c * N + P] * m->Sf[c * M + fb];
+            double a = w->rAU[P] * m->magSf[fb] * m->delta[fb];
+            w->af[fb] = a;
+            w->pdiag[P] += a;
+            w->pb[P] += a * cs->pb[b];
+        }
+        w->phis[fb] = ph;
+        w->pb[P] -= ph;
+    }
+    if (ref_cell >= 0) {
+        w->pb[ref_cell] += w->pdiag[ref_cell] * p_ref;
+        w->pdiag[ref_cell] *= 2.0;
+    }
+}
+
+static void correct_flux(ocase *cs, const pwork *w)
+{
+    const omesh *m = cs->m;
+    int F = m->F, B = m->B;
+    const double *p = cs->p;
+    for (int f = 0; f < F; ++f)
+        cs->phi[f] = w->phis[f] - w->af[f] * (p[m->nei[f]] - p[m->own[f]]) - w->nof[f];
+    for (int b = 0; b < B; ++b) {
+        int fb = F + b;
+        int t = m->patch[m->bpatch[b]].type;
+        if (t == P_EMPTY) cs->phi[fb] = 0.0;
+        else if (t == P_OUTLET) cs->phi[fb] = w->phis[fb] - w->af[fb] * (cs->pb[b] - p[m->own[fb]]);
+        else cs->phi[fb] = w->phis[fb];
+    }
+}
+
+/* max_P | sum_out phi_P + (b - A p)_P + pin_P | / max|b|; identity of the
+ * flux correction (pin_P = diag_r/2 (p_r - p_ref) at the reference cell). */
+static double continuity_identity(const ocase *cs, const pwork *w, int ref_cell, double p_ref)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F, B = m->B;
+    double *div = xcalloc(N, sizeof(double)), *Ap = xcalloc(N, sizeof(double));
+    for (int f = 0; f < F; ++f) { div[m->own[f]] += cs->phi[f]; div[m->nei[f]] -= cs->phi[f]; }
+    for (int b = 0; b < B; ++b) div[m->own[F + b]] += cs->phi[F + b];
+    ldu_matvec(N, F, m->own, m->nei, w->pdiag, w->pup, w->pup, cs->p, Ap);
+    double mb = 0.0, me = 0.0;
+    for (int i = 0; i < N; ++i) if (fabs(w->pb[i]) > mb) mb = fabs(w->pb[i]);
+    for (int i = 0; i < N; ++i) {
+        double e = div[i] + (w->pb[i] - Ap[i]);
+        if (i == ref_cell) e += 0.5 * w->pdiag[i] * (cs->p[i] - p_ref);
+        if (fabs(e) > me) me = fabs(e);
+    }
+    free(div); free(Ap);
+    return mb > 0.0 ? me / mb : me;
+}
+
+static void correct_velocity(ocase *cs, const pwork *w, double *gradp)
+{
+    const omesh *m = cs->m;
+    int N = m->N;
+    grad_p(cs, cs->p, gradp);
+    for (int c = 0; c < 3; ++c)
+        for (int i = 0; i < N; ++i)
+            cs->u[c * N + i] = w->HbyA[c * N + i] - w->rAU[i] * gradp[c * N + i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* PISO time step (paper Sec. 3): momentum predictor, then n_corr pressure   */
+/* corrections.  M is assembled once per step; H uses the current u.         */
+/* Per-solve statistics: iters[0..2] momentum components, iters[3..] p;      */
+/* res[2k] initial and res[2k+1] final normalised residual of solve k.       */
+/* Returns 0, or the first non-zero solver status.                            */
+/* ------------------------------------------------------------------------ */
+
+int orc_piso_step(ocase *cs, double dt, int n_corr, double p_tol, int p_maxit, double u_tol,
+                  int u_maxit, int ref_orig, double p_ref, int *iters, double *res,
+                  double *cont_err)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F;
+    int ref = ref_orig >= 0 ? m->cell_new_of_old[ref_orig] : -1;
+    int status = 0, st;
+    double *gradp = xcalloc(3 * (size_t)N, sizeof(double));
+    double *gU = m->nonorth ? xcalloc(9 * (size_t)N, sizeof(double)) : NULL;
+    double *mdiag = xcalloc(N, sizeof(double)), *up = xcalloc(F ? F : 1, sizeof(double));
+    double *lo = xcalloc(F ? F : 1, sizeof(double)), *src = xcalloc(3 * (size_t)N, sizeof(double));
+    double *rhs = xcalloc(N, sizeof(double));
+    pwork w;
+    pwork_alloc(&w, m);
+
+    grad_p(cs, cs->p, gradp);
+    if (gU) grad_u(cs, gU);
+    assemble_momentum(cs, 1, dt, 1.0, gU, mdiag, up, lo, src);
+    for (int c = 0; c < 3; ++c) {
+        for (int i = 0; i < N; ++i) rhs[i] = src[c * N + i] - m->V[i] * gradp[c * N + i];
+        st = orc_bicgstab(N, F, m->own, m->nei, mdiag, up, lo, rhs, cs->u + (size_t)c * N,
+                          u_tol, 0.0, u_maxit, &res[2 * c], &res[2 * c + 1], &iters[c]);
+        if (st && !status) status = st;
+    }
+    *cont_err = 0.0;
+    for (int k = 0; k < n_corr; ++k) {
+        compute_HbyA(cs, mdiag, up, lo, src, &w);
+        assemble_pressure(cs, gradp, ref, p_ref, &w);
+        st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, 0.0, p_maxit,
+                     &res[2 * (3 + k)], &res[2 * (3 + k) + 1], &iters[3 + k]);
+        if (st && !status) status = st;
+        correct_flux(cs, &w);
+        double ce = continuity_identity(cs, &w, ref, p_ref);
+        if (ce > *cont_err) *cont_err = ce;
+        correct_velocity(cs, &w, gradp);
+    }
+    pwork_free(&w);
+    free(gradp); free(gU); free(mdiag); free(up); free(lo); free(src); free(rhs);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SIMPLE iteration (paper Sec. 3).  READINGS: implicit momentum relaxation  */
+/* alpha_u; one pressure solve; the flux is corrected with the unrelaxed    */
+/* pressure; then p <- p_old + alpha_p (p_sol - p_old) and                    */
+/* u = HbyA - rAU grad p_relaxed.  Outer convergence measure init_res_max =   */
+/* max of                                                                      */
+/*   max_c ||b_c - M u_c||_2 / max_c ||b_c||_2   (momentum, before the solve) */
+/*   ||b_p - A p||_2 / ||phi*||_2                (pressure, before the solve) */
+/* i.e. each equation's initial residual scaled by a quantity that does not   */
+/* vanish when a component of the exact solution is zero.                     */
+/* ------------------------------------------------------------------------ */
+
+int orc_simple_iter(ocase *cs, double alpha_u, double alpha_p, double p_tol, double p_reltol,
+                    int p_maxit, double u_tol, double u_reltol, int u_maxit, int ref_orig,
+                    double p_ref, int *iters, double *res, double *cont_err, double *init_res_max)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F;
+    int ref = ref_orig >= 0 ? m->cell_new_of_old[ref_orig] : -1;
+    int status = 0, st;
+    double *gradp = xcalloc(3 * (size_t)N, sizeof(double));
+    double *gU = m->nonorth ? xcalloc(9 * (size_t)N, sizeof(double)) : NULL;
+    double *mdiag = xcalloc(N, sizeof(double)), *up = xcalloc(F ? F : 1, sizeof(double));
+    double *lo = xcalloc(F ? F : 1, sizeof(double)), *src = xcalloc(3 * (size_t)N, sizeof(double));
+    double *rhs = xcalloc(N, sizeof(double)), *pold = xcalloc(N, sizeof(double));
+    pwork w;
+    pwork_alloc(&w, m);
+    double irm = 0.0;
+
+    grad_p(cs, cs->p, gradp);
+    if (gU) grad_u(cs, gU);
+    assemble_momentum(cs, 0, 1.0, alpha_u, gU, mdiag, up, lo, src);
+    double bmax = 0.0, rmax = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        for (int i = 0; i < N; ++i) rhs[i] = src[c * N + i] - m->V[i] * gradp[c * N + i];
+        ldu_matvec(N, F, m->own, m->nei, mdiag, up, lo, cs->u + (size_t)c * N, pold);
+        for (int i = 0; i < N; ++i) pold[i] = rhs[i] - pold[i];
+        double nb = norm2_n(N, rhs), nr = norm2_n(N, pold);
+        if (nb > bmax) bmax = nb;
+        if (nr > rmax) rmax = nr;
+        st = orc_bicgstab(N, F, m->own, m->nei, mdiag, up, lo, rhs, cs->u + (size_t)c * N,
+                          u_tol, u_reltol, u_maxit, &res[2 * c], &res[2 * c + 1], &iters[c]);
+        if (st && !status) status = st;
+    }
+    if (bmax > 0.0) irm = rmax / bmax;
+    compute_HbyA(cs, mdiag, up, lo, src, &w);
+    assemble_pressure(cs, gradp, ref, p_ref, &w);
+    {
+        ldu_matvec(N, F, m->own, m->nei, w.pdiag, w.pup, w.pup, cs->p, pold);
+        for (int i = 0; i < N; ++i) pold[i] = w.pb[i] - pold[i];
+        double nr = norm2_n(N, pold), nphi = norm2_n(F + m->B, w.phis);
+        double rp = nphi > 0.0 ? nr / nphi : nr;
+        if (rp > irm) irm = rp;
+    }
+    memcpy(pold, cs->p, sizeof(double) * N);
+    st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, p_reltol, p_maxit,
+                 &res[6], &res[7], &iters[3]);
+    if (st && !status) status = st;
+    correct_flux(cs, &w);
+    *cont_err = continuity_identity(cs, &w, ref, p_ref);
+    for (int i = 0; i < N; ++i) cs->p[i] = pold[i] + alpha_p * (cs->p[i] - pold[i]);
+    correct_velocity(cs, &w, gradp);
+    *init_res_max = irm;
+    pwork_free(&w);
+    free(gradp); free(gU); free(mdiag); free(up); free(lo); free(src); free(rhs); free(pold);
+    return status;
+}
+
+/* Pressure system of the first PISO corrector from the current state (used
+ * by the Krylov pins): returns diag [N], upper [F], b [N] in internal order. */
+void orc_case_pressure_system(ocase *cs, double dt, int ref_orig, double p_ref, double *pdiag,
+                              double *pup, double *pb)
+{
+    const omesh *m = cs->m;
+    int N = m->N, F = m->F;
+    int ref = ref_orig >= 0 ? m->cell_new_of_old[ref_orig] : -1;
+    double *gradp = xcalloc(3 * (size_t)N, sizeof(double));
+    double *gU = m->nonorth ? xcalloc(9 * (size_t)N, sizeof(double)) : NULL;
+    double *mdiag = xcalloc(N, sizeof(double)), *up = xcalloc(F ? F : 1, sizeof(double));
+    double *lo = xcalloc(F ? F : 1, sizeof(double)), *src = xcalloc(3 * (size_t)N, sizeof(double));
+    pwork w;
+    pwork_alloc(&w, m);
+    grad_p(cs, cs->p, gradp);
+    if (gU) grad_u(cs, gU);
+    assemble_momentum(cs, 1, dt, 1.0, gU, mdiag, up, lo, src);
+    compute_HbyA(cs, mdiag, up, lo, src, &w);
+    assemble_pressure(cs, gradp, ref, p_ref, &w);
+    memcpy(pdiag, w.pdiag, sizeof(double) * N);
+    memcpy(pup, w.pup, sizeof(double) * F);
+    memcpy(pb, w.pb, sizeof(double) * N);
+    pwork_free(&w);
+    free(gradp); free(gU); free(mdiag); free(up); free(lo); free(src);
+}
+
+/* Scalar Laplacian with Dirichlet boundary values (manufactured-solution
+ * pin of the face-gradient discretisation, Sec. 4.3.3 "Laplacian"):
+ * assembles  -div(grad x) V-integrated with x_b given on every non-empty
+ * boundary face, non-orthogonal correction with the gradient of xg (lagged),
+ * as diag [N], upper [F], b [N]. */
+void orc_laplacian_system(const omesh *m, const double *xb, const double *gradx, double *diag,
+                          double *upper, double *b)
+{
+    int N = m->N, F = m->F, B = m->B;
+    for (int i = 0; i < N; ++i) { diag[i] = 0.0; b[i] = 0.0; }
+    for (int f = 0; f < F; ++f) {
+        int P = m->own[f], Q = m->nei[f];
+        double a = m->magSf[f] * m->delta[f];
+        diag[P] += a; diag[Q] += a; upper[f] = -a;
+        if (m->nonorth && gradx) {
+            double kg = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double gf = m->w[f] * gradx[d * N + P] + (1.0 - m->w[f]) * gradx[d * N + Q];
+                kg += m->kv[d * F + f] * gf;
+            }
+            double nf = m->magSf[f] * kg;
+            b[P] += nf; b[Q] -= nf;
+        }
+    }
+    for (int q = 0; q < B; ++q) {
+        int fb = F + q, P = m->own[fb];
+        if (m->patch[m->bpatch[q]].type == P_EMPTY) continue;
+        double a = m->magSf[fb] * m->delta[fb];
+        diag[P] += a;
+        b[P] += a * xb[q];
+    }
+}
+
+/* Gauss gradient of a cell field with given boundary values (internal order). */
+void orc_gauss_grad(const omesh *m, const double *x, const double *xb, double *g)
+{
+    gauss_grad(m, x, xb, g);
+}
+
+/* internal-order state access for tests */
+void orc_case_state(const ocase *cs, double *u, double *p, double *phi)
+{
+    const omesh *m = cs->m;
+    memcpy(u, cs->u, sizeof(double) * 3 * m->N);
+    memcpy(p, cs->p, sizeof(double) * m->N);
+    memcpy(phi, cs->phi, sizeof(double) * (m->F + m->B));
+}
