@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: PISO time steps of the 3-D lid-driven cavity on one GB300.
+
+Default workload: the 100^3 = 1M-cell cavity (unit cube, lid u = 1,
+nu = 0.01, dt = 0.002, 2 pressure correctors, pressure CG to 1e-6 relative
+residual, FP64), cells permuted with seed 1234 and renumbered by reverse
+Cuthill-McKee.  One "step" is one full PISO time step: momentum assembly,
+three BiCGStab momentum solves, and two pressure corrections (H/A, pressure
+assembly, Jacobi-PCG, flux and velocity correction).
+
+The timed steps start from rest, after W untimed warm-up steps on the same
+case; L2 is flushed (256 MiB write) between timed steps, outside the timed
+windows.  Device time is taken with CUDA events on the library's stream.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle
+instead (a bounded sample of the same workload, see ``REF_SAMPLE``).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PISO steps/s & cell-updates/s; pressure-CG HBM GB/s vs peak; mixed vs FP64"
+UNIT = "cell-updates/s"
+
+WORKLOADS = {
+    "cavity3d_100": dict(n=100, dim=3, nu=0.01, dt=0.002, n_corr=2, seed=1234),
+    "cavity3d_200": dict(n=200, dim=3, nu=0.01, dt=0.001, n_corr=2, seed=1234),
+    "cavity3d_40": dict(n=40, dim=3, nu=0.01, dt=0.002, n_corr=2, seed=1234),
+    "cavity2d_20": dict(n=20, dim=2, nu=0.1, dt=0.005, n_corr=2, seed=None),
+}
+# bounded sample of the cavity used for the CPU reference arm
+REF_SAMPLE = "cavity3d_40"
+
+# ncu DRAM traffic (read + write bytes) per k_pcg launch, measured on the
+# workload named here; valid only for the kernel source it was taken on
+PCG_TRAFFIC = {"source_sha1": None, "bytes_per_iter": None, "workload": None}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_mesh(w):
+    import meshgen as mg
+    if w["dim"] == 2:
+        return mg.cavity2d(w["n"])
+    m = mg.cavity3d(w["n"])
+    if w["seed"] is not None:
+        m = mg.permute_cells(m, mg.random_permutation(m.n_cells, w["seed"]))
+    return m
+
+
+def cg_bytes_per_iter(N, F):
+    """Algorithmic bytes of one Jacobi-PCG iteration (FP64 values, int32
+    indices): SMVP + p.q reads diag, upper, owner/neighbour and p and writes
+    q (24N + 16F); the r update with r.z reads q, r, 1/diag and writes r
+    (32N); the x and p updates read x, p, r, 1/diag and write x, p (48N)."""
+    return 104 * N + 16 * F
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v, device):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def source_sha1():
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_1207_1571_gb300", "csrc", "krylov.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import ctypes as C
+    from paper_1207_1571_gb300 import build as B
+    import paper_1207_1571_gb300 as P
+    from paper_1207_1571_gb300 import _capi
+
+    if ws == 1:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.build()
+    L = P.load()
+    w = WORKLOADS[args.workload]
+    m = make_mesh(w)
+    N, F = m.n_cells, m.n_internal_faces
+    mesh = P.Mesh(m, renumber=True)
+    case = P.Case(mesh, w["nu"])
+    ref = m.corner_cell
+    prm = case.piso_params(w["dt"], w["n_corr"], p_ref_cell=ref)
+    stream = mesh.stream
+    zero = (torch.zeros(3, N, dtype=torch.float64, device="cuda"),
+            torch.zeros(N, dtype=torch.float64, device="cuda"),
+            torch.zeros(m.n_faces, dtype=torch.float64, device="cuda"))
+    st = _capi.fv_step_stats()
+
+    def step(with_stats=True):
+        rc = L.fv_piso_step(case.h, C.byref(prm), C.byref(st) if with_stats else None)
+        _capi.check(rc, "fv_piso_step", allow=(4,))
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    case.set_fields(*zero)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    L.fv_profile_read(None, None, 1)
+    L.fv_profile_enable(1)
+    iters_p, iters_u, statuses = 0, 0, []
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[k][0].record(stream)
+            step(with_stats=False)
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+            # statistics of this step, read after its end event (synchronises)
+            stats = case.last_stats()
+            iters_p += sum(stats["iters"][3:])
+            iters_u += sum(stats["iters"][:3])
+            statuses.append(stats["status"])
+        torch.cuda.synchronize()
+    barrier(ws)
+    L.fv_profile_enable(0)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(ms_steps) / 1e3
+    prof_ms = (C.c_double * 7)()
+    prof_n = (C.c_int64 * 7)()
+    L.fv_profile_read(prof_ms, prof_n, 1)
+    t = allmax(ws, t_local, "cuda")
+    value = ws * N * args.steps / t
+    pcg_s = prof_ms[4] / 1e3
+    bpi = cg_bytes_per_iter(N, F)
+    peak, peak_kind = peaks()
+    achieved = bpi * iters_p / pcg_s / 1e9 if pcg_s > 0 else None
+    traffic = None
+    if PCG_TRAFFIC["source_sha1"] == source_sha1() and PCG_TRAFFIC["bytes_per_iter"]:
+        traffic = PCG_TRAFFIC["bytes_per_iter"] * iters_p / args.steps / (2 * 1.0)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        case.set_fields(*zero)
+        torch.cuda.synchronize()
+        hu, hp, hphi = np.zeros((3, N)), np.zeros(N), np.zeros(m.n_faces)
+        te = 0.0
+        for k in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            _capi.check(L.fv_case_set_fields_host(case.h, hu.ctypes.data, hp.ctypes.data,
+                                                  hphi.ctypes.data, 1), "set_fields_host")
+            step(with_stats=False)
+            _capi.check(L.fv_case_get_fields_host(case.h, hu.ctypes.data, hp.ctypes.data,
+                                                  hphi.ctypes.data, 1), "get_fields_host")
+            te += time.perf_counter() - t0
+        te = allmax(ws, te, "cuda")
+        nbytes = 8 * (3 * N + N + m.n_faces)
+        e2e = {"value": ws * N * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps_per_s": args.steps / t,
+        "config": {"workload": f"{args.workload}: 3-D lid-driven cavity {w['n']}^3 hex cells"
+                   if w["dim"] == 3 else f"{args.workload}: 2-D lid-driven cavity",
+                   "cells": N, "internal_faces": F, "nu": w["nu"], "dt": w["dt"],
+                   "n_corr": w["n_corr"], "p_tol": 1e-6, "renumbering": "seed-1234 permutation + RCM",
+                   "l2": "flushed (256 MiB write) between timed steps; steps timed from rest",
+                   "parallelism": "replicas only" if ws > 1 else "1 GPU"},
+        "cg": {"iterations": iters_p, "iters_per_step": iters_p / args.steps,
+               "bicgstab_iterations": iters_u, "ms": prof_ms[4],
+               "share_of_step": prof_ms[4] / (1e3 * t_local) if t_local > 0 else None},
+        "stages_ms": {n: prof_ms[k] for k, n in enumerate(_capi.PROF_STAGES)},
+        "roofline": {"bound": "hbm", "kernel": "k_pcg", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "bytes_per_iter": bpi, "algorithmic": "104N+16F bytes per CG iteration"},
+        "gpu_launches": int(sum(prof_n[k] for k in range(7))),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "memory_bytes": case.memory_bytes(),
+        "statuses": sorted(set(statuses)),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload)
+    return out
+
+
+def cpu_baseline(workload):
+    """The oracle as it stands, single thread, one PISO step of the same
+    workload from rest (the first step of the timed sequence)."""
+    import oracle as O
+    w = WORKLOADS[workload]
+    m = make_mesh(w)
+    om = O.Mesh(m, renumber=True)
+    oc = O.Case(om, w["nu"])
+    t0 = time.perf_counter()
+    oc.piso_step(w["dt"], w["n_corr"], p_ref_cell=m.corner_cell)
+    t = time.perf_counter() - t0
+    return {"value": m.n_cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 PISO step from rest of {workload} ({m.n_cells} cells), "
+                      f"single-threaded FP64 C oracle, {t:.1f} s"}
+
+
+# ------------------------------------------------------------- reference --
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle as O
+    w = WORKLOADS[REF_SAMPLE]
+    m = make_mesh(w)
+    om = O.Mesh(m, renumber=True)
+    oc = O.Case(om, w["nu"])
+    for _ in range(args.warmup):
+        oc.piso_step(w["dt"], w["n_corr"], p_ref_cell=m.corner_cell)
+    oc.set_fields(np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_faces))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oc.piso_step(w["dt"], w["n_corr"], p_ref_cell=m.corner_cell)
+    t = time.perf_counter() - t0
+    v = m.n_cells * args.steps / t
+    sample = (f"{args.steps} PISO steps from rest of the {w['n']}^3 cavity sample "
+              f"({m.n_cells} cells; the CG iteration count per step grows with n, so this "
+              f"overstates the oracle's rate on the 100^3 workload), single-threaded FP64 C oracle")
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{args.workload} (timed on the {REF_SAMPLE} sample)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cavity3d_100")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,577 @@
+// krylov.cu -- persistent, cooperative Krylov solvers (paper Sec. 3:
+// Jacobi-preconditioned CG for pressure, Jacobi-preconditioned BiCGStab for
+// momentum; Sec. 4.3.2: SMVP, daxpy, dot product, reduction and diagonal
+// preconditioner are the building blocks).
+//
+// One launch runs a whole solve.  The grid is sized to be co-resident
+// (cooperative launch); phases are separated by a grid barrier that spins a
+// bounded number of times and otherwise records FV_E_TIMEOUT.  Reductions
+// are deterministic: each block writes its partial sums, and after the
+// barrier every block adds all partials in the same fixed order, so every
+// block takes the same decisions (convergence, breakdown) from bit-identical
+// scalars.  Rows are owned by a fixed thread for the whole solve, so a
+// thread only reads other threads' data where the algorithm needs neighbour
+// values (matrix-vector products); those loads bypass L1 (__ldcg).
+//
+// CG works on the symmetrically scaled system  D^-1/2 A D^-1/2 y = D^-1/2 b
+// with x = D^-1/2 y: in exact arithmetic this generates the same iterates,
+// step lengths and residual norms as Jacobi-preconditioned CG on A x = b
+// (z = D^-1 r becomes the identity and r.z becomes r^.r^), while the product
+// needs no diagonal and the preconditioner no extra pass.  The stopping test
+// uses the unscaled residual ||r||_2 = ||D^1/2 r^||_2, exactly as the
+// unscaled method does.
+#include <cooperative_groups.h>
+
+#include "fvgb_internal.h"
+
+namespace fvgb {
+
+long long g_spin_limit = 1LL << 25;
+constexpr int kBlock = 512;
+constexpr int kParts = 8;       // doubles per block per partial record
+
+struct RowSpan {
+    int e0, K;
+};
+
+__device__ __forceinline__ RowSpan row_span(const int32_t *__restrict__ slice_ptr, int i)
+{
+    const int s = i >> 5;
+    const int p0 = slice_ptr[s], p1 = slice_ptr[s + 1];
+    return {p0 + (i & 31), (p1 - p0) >> 5};
+}
+
+// ------------------------------------------------------------ barriers --
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Returns false (for every thread of the block) when the barrier gave up or
+// another block recorded an error.
+__device__ bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (gridDim.x == 1) return true;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicExch(&bar->gen, g + 1);
+        } else {
+            long long spins = 0;
+            while (ld_acquire(&bar->gen) == g) {
+                if (++spins > limit) {
+                    atomicExch(&bar->err, FV_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 256) __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)&bar->err != 0) ok = 0;
+        s_ok = ok;
+    }
+    ++gen;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV])
+{
+    __shared__ double red[NV][kBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][wid] = x;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = lane < kBlock / 32 ? red[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) red[k][0] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = red[k][0];
+    __syncthreads();
+}
+
+// Sum v over the grid; every block returns the same bits.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &gen, long long limit)
+{
+    block_sum<NV>(v);
+    if (gridDim.x == 1) return true;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[blockIdx.x * kParts + k] = v[k];
+    }
+    if (!grid_sync(bar, gen, limit)) return false;
+    double w[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = 0.0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += kBlock) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] += __ldcg(part + j * kParts + k);
+    }
+    block_sum<NV>(w);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = w[k];
+    return true;
+}
+
+// ------------------------------------------------------------------ CG --
+
+struct CgArgs {
+    int N;
+    const int32_t *slice_ptr, *col;
+    double *val;
+    const double *diag, *b;
+    double *x, *s, *r, *p, *q, *y;
+    double *partA, *partB;
+    GridBar *bar;
+    long long spin;
+    double tol, reltol;
+    int maxit;
+    DevSolveStats *stats;
+};
+
+__global__ void __launch_bounds__(kBlock, 2) k_pcg(CgArgs a)
+{
+    const int N = a.N;
+    const int stride = gridDim.x * kBlock;
+    const int i0 = blockIdx.x * kBlock + threadIdx.x;
+    unsigned gen = 0;
+    bool ok = true;
+    int status = FV_OK, it = 0;
+    double nb = 0.0, nr0 = 0.0, nr = 0.0;
+
+    // S1: scaling s = D^-1/2 and scaled start y = D^1/2 x
+    for (int i = i0; i < N; i += stride) {
+        const double d = a.diag[i];
+        const double sq = sqrt(d);
+        a.s[i] = 1.0 / sq;
+        a.y[i] = a.x[i] * sq;
+    }
+    ok = grid_sync(a.bar, gen, a.spin);
+    // S2: scale the off-diagonals, r^ = s (b - A x), norms
+    double v3[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||r||^2, r^.r^
+    if (ok) {
+        for (int i = i0; i < N; i += stride) {
+            const RowSpan rs = row_span(a.slice_ptr, i);
+            const double si = a.s[i], d = a.diag[i], xi = a.x[i];
+            double ax = d * xi;
+            for (int k = 0; k < rs.K; ++k) {
+                const int e = rs.e0 + 32 * k;
+                const int c = a.col[e];
+                const double v = a.val[e];
+                ax += v * __ldcg(a.x + c);
+                a.val[e] = v * si * __ldcg(a.s + c);
+            }
+            const double bi = a.b[i];
+            const double rh = si * (bi - ax);
+            a.r[i] = rh;
+            v3[0] += bi * bi;
+            v3[1] += d * rh * rh;
+            v3[2] += rh * rh;
+        }
+        ok = grid_sum<3>(v3, a.partB, a.bar, gen, a.spin);
+    }
+    double thresh = 0.0, rho = v3[2];
+    if (ok) {
+        nb = sqrt(v3[0]);
+        nr0 = sqrt(v3[1]);
+        nr = nr0;
+        thresh = fmax(a.tol * nb, a.reltol * nr0);
+    }
+    if (ok && nb == 0.0) {
+        for (int i = i0; i < N; i += stride) a.x[i] = 0.0;
+        nr0 = nr = 0.0;
+    } else if (ok && nr0 > thresh) {
+        double alpha = 0.0, beta = 0.0;
+        bool done = false;
+        while (!done) {
+            ++it;
+            // P1: p = r^ + beta p (first: p = r^); y += alpha_prev p_prev
+            for (int i = i0; i < N; i += stride) {
+                const double ri = a.r[i];
+                if (it == 1) {
+                    a.p[i] = ri;
+                } else {
+                    const double po = a.p[i];
+                    a.y[i] += alpha * po;
+                    a.p[i] = ri + beta * po;
+                }
+            }
+            if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+            // P2: q = A^ p (unit diagonal), p.q
+            double v1[1] = {0.0};
+            for (int i = i0; i < N; i += stride) {
+                const RowSpan rs = row_span(a.slice_ptr, i);
+                const double pi = a.p[i];
+                double acc = pi;
+                for (int k = 0; k < rs.K; ++k) {
+                    const int e = rs.e0 + 32 * k;
+                    acc += a.val[e] * __ldcg(a.p + a.col[e]);
+                }
+                a.q[i] = acc;
+                v1[0] += pi * acc;
+            }
+            if (!(ok = grid_sum<1>(v1, a.partA, a.bar, gen, a.spin))) break;
+            const double pq = v1[0];
+            if (!(pq > 0.0) || !isfinite(pq)) { status = FV_E_DIVERGED; alpha = 0.0; break; }
+            alpha = rho / pq;
+            // P3: r^ -= alpha q; r^.r^ and ||D^1/2 r^||^2
+            double v2[2] = {0.0, 0.0};
+            for (int i = i0; i < N; i += stride) {
+                const double ri = a.r[i] - alpha * a.q[i];
+                a.r[i] = ri;
+                v2[0] += ri * ri;
+                v2[1] += a.diag[i] * ri * ri;
+            }
+            if (!(ok = grid_sum<2>(v2, a.partB, a.bar, gen, a.spin))) break;
+            nr = sqrt(v2[1]);
+            if (!isfinite(nr)) { status = FV_E_DIVERGED; break; }
+            if (nr <= thresh) { done = true; break; }
+            if (it >= a.maxit) { status = FV_E_NOT_CONVERGED; done = true; break; }
+            beta = v2[0] / rho;
+            rho = v2[0];
+        }
+        if (ok) {
+            // final update of the scaled iterate, then x = D^-1/2 y
+            const double af = (status == FV_E_DIVERGED) ? 0.0 : alpha;
+            for (int i = i0; i < N; i += stride) {
+                const double yi = a.y[i] + af * a.p[i];
+                a.x[i] = a.s[i] * yi;
+            }
+        }
+    }
+    if (!ok) status = FV_E_TIMEOUT;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.stats->iters = it;
+        a.stats->status = status;
+        a.stats->res0 = nb > 0.0 ? nr0 / nb : 0.0;
+        a.stats->res = nb > 0.0 ? nr / nb : 0.0;
+    }
+}
+
+// ------------------------------------------------------------ BiCGStab --
+
+struct BicgArgs {
+    int N, ncomp;
+    const int32_t *slice_ptr, *col;
+    const double *val, *diag, *b, *src, *gradp, *V;
+    double *x, *dinv;
+    double *r, *rh, *p, *v, *y, *s, *z, *t;   // [ncomp][N]
+    double *partA, *partB;
+    GridBar *bar;
+    long long spin;
+    double tol, reltol;
+    int maxit;
+    DevSolveStats *stats;
+};
+
+__device__ __forceinline__ double spmv_row(const BicgArgs &a, int i, double d, const double *vec)
+{
+    const RowSpan rs = row_span(a.slice_ptr, i);
+    double acc = d * vec[i];
+    for (int k = 0; k < rs.K; ++k) {
+        const int e = rs.e0 + 32 * k;
+        acc += a.val[e] * __ldcg(vec + a.col[e]);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
+{
+    const int N = a.N, nc = a.ncomp;
+    const size_t NN = (size_t)N;
+    const int stride = gridDim.x * kBlock;
+    const int i0 = blockIdx.x * kBlock + threadIdx.x;
+    unsigned gen = 0;
+    bool ok = true;
+
+    // S: r = b - A x, rh = r, norms per component
+    double v6[6] = {0, 0, 0, 0, 0, 0};   // ||b_c||^2, ||r_c||^2
+    for (int i = i0; i < N; i += stride) {
+        const double d = a.diag[i];
+        a.dinv[i] = 1.0 / d;
+        for (int c = 0; c < nc; ++c) {
+            const double bi = a.b ? a.b[c * NN + i] : a.src[c * NN + i] - a.V[i] * a.gradp[c * NN + i];
+            const double ri = bi - spmv_row(a, i, d, a.x + c * NN);
+            a.r[c * NN + i] = ri;
+            a.rh[c * NN + i] = ri;
+            v6[2 * c] += bi * bi;
+            v6[2 * c + 1] += ri * ri;
+        }
+    }
+    ok = grid_sum<6>(v6, a.partB, a.bar, gen, a.spin);
+    double nb[3] = {0, 0, 0}, nr0[3] = {0, 0, 0}, nr[3] = {0, 0, 0}, thr[3] = {0, 0, 0};
+    double rho[3] = {1, 1, 1}, rho_old[3] = {1, 1, 1}, alpha[3] = {1, 1, 1}, omega[3] = {1, 1, 1};
+    int active[3] = {0, 0, 0}, zero[3] = {0, 0, 0}, iters[3] = {0, 0, 0}, status[3] = {0, 0, 0};
+    int n_active = 0;
+    if (ok) {
+        for (int c = 0; c < nc; ++c) {
+            nb[c] = sqrt(v6[2 * c]);
+            nr0[c] = nr[c] = sqrt(v6[2 * c + 1]);
+            thr[c] = fmax(a.tol * nb[c], a.reltol * nr0[c]);
+            rho[c] = v6[2 * c + 1];
+            if (nb[c] == 0.0) { zero[c] = 1; nr0[c] = nr[c] = 0.0; }
+            else if (nr0[c] > thr[c]) { active[c] = 1; ++n_active; }
+        }
+        for (int c = 0; c < nc; ++c)
+            if (zero[c])
+                for (int i = i0; i < N; i += stride) a.x[c * NN + i] = 0.0;
+    }
+    int it = 0;
+    while (ok && n_active > 0) {
+        ++it;
+        // P1: p = r + beta (p - omega v); y = D^-1 p
+        double beta[3];
+        for (int c = 0; c < nc; ++c) beta[c] = (rho[c] / rho_old[c]) * (alpha[c] / omega[c]);
+        for (int i = i0; i < N; i += stride) {
+            const double di = a.dinv[i];
+            for (int c = 0; c < nc; ++c) {
+                if (!active[c]) continue;
+                const size_t j = c * NN + i;
+                const double pn = (it == 1) ? a.r[j] : a.r[j] + beta[c] * (a.p[j] - omega[c] * a.v[j]);
+                a.p[j] = pn;
+                a.y[j] = pn * di;
+            }
+        }
+        if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+        // P2: v = A y; rh.v
+        double v3[3] = {0, 0, 0};
+        for (int i = i0; i < N; i += stride) {
+            const double d = a.diag[i];
+            for (int c = 0; c < nc; ++c) {
+                if (!active[c]) continue;
+                const size_t j = c * NN + i;
+                const double vi = spmv_row(a, i, d, a.y + c * NN);
+                a.v[j] = vi;
+                v3[c] += a.rh[j] * vi;
+            }
+        }
+        if (!(ok = grid_sum<3>(v3, a.partA, a.bar, gen, a.spin))) break;
+        for (int c = 0; c < nc; ++c) {
+            if (!active[c]) continue;
+            if (v3[c] == 0.0 || !isfinite(v3[c])) {
+                status[c] = FV_E_DIVERGED; iters[c] = it; active[c] = 0; --n_active;
+            } else {
+                alpha[c] = rho[c] / v3[c];
+            }
+        }
+        // P3: s = r - alpha v; z = D^-1 s
+        for (int i = i0; i < N; i += stride) {
+            const double di = a.dinv[i];
+            for (int c = 0; c < nc; ++c) {
+                if (!active[c]) continue;
+                const size_t j = c * NN + i;
+                const double si = a.r[j] - alpha[c] * a.v[j];
+                a.s[j] = si;
+                a.z[j] = si * di;
+            }
+        }
+        if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+        // P4: t = A z; t.s, t.t
+        double w6[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = i0; i < N; i += stride) {
+            const double d = a.diag[i];
+            for (int c = 0; c < nc; ++c) {
+                if (!active[c]) continue;
+                const size_t j = c * NN + i;
+                const double ti = spmv_row(a, i, d, a.z + c * NN);
+                a.t[j] = ti;
+                w6[2 * c] += ti * a.s[j];
+                w6[2 * c + 1] += ti * ti;
+            }
+        }
+        if (!(ok = grid_sum<6>(w6, a.partB, a.bar, gen, a.spin))) break;
+        for (int c = 0; c < nc; ++c)
+            if (active[c]) omega[c] = w6[2 * c + 1] > 0.0 ? w6[2 * c] / w6[2 * c + 1] : 0.0;
+        // P5: x += alpha y + omega z; r = s - omega t; rh.r, r.r
+        double u6[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = i0; i < N; i += stride) {
+            for (int c = 0; c < nc; ++c) {
+                if (!active[c]) continue;
+                const size_t j = c * NN + i;
+                a.x[j] += alpha[c] * a.y[j] + omega[c] * a.z[j];
+                const double ri = a.s[j] - omega[c] * a.t[j];
+                a.r[j] = ri;
+                u6[2 * c] += a.rh[j] * ri;
+                u6[2 * c + 1] += ri * ri;
+            }
+        }
+        if (!(ok = grid_sum<6>(u6, a.partA, a.bar, gen, a.spin))) break;
+        for (int c = 0; c < nc; ++c) {
+            if (!active[c]) continue;
+            nr[c] = sqrt(u6[2 * c + 1]);
+            int stop = 0;
+            if (!isfinite(nr[c])) { status[c] = FV_E_DIVERGED; stop = 1; }
+            else if (nr[c] <= thr[c]) { stop = 1; }
+            else if (it >= a.maxit) { status[c] = FV_E_NOT_CONVERGED; stop = 1; }
+            else if (omega[c] == 0.0) { status[c] = FV_E_DIVERGED; stop = 1; }
+            if (stop) { iters[c] = it; active[c] = 0; --n_active; }
+            rho_old[c] = rho[c];
+            rho[c] = u6[2 * c];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int c = 0; c < nc; ++c) {
+            a.stats[c].iters = iters[c];
+            a.stats[c].status = ok ? status[c] : FV_E_TIMEOUT;
+            a.stats[c].res0 = nb[c] > 0.0 ? nr0[c] / nb[c] : 0.0;
+            a.stats[c].res = nb[c] > 0.0 ? nr[c] / nb[c] : 0.0;
+        }
+    }
+}
+
+// ------------------------------------------------------------ launches --
+
+static fv_status coop_launch(const void *fn, int G, void **args, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FV_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    return FV_OK;
+}
+
+static int grid_for(const fv_mesh *m, int rows)
+{
+    // about 4 rows per thread at least before another block is worth a
+    // grid-wide barrier; never more blocks than can be co-resident
+    int want = (rows + 4 * kBlock - 1) / (4 * kBlock);
+    if (want < 1) want = 1;
+    return want < m->kw.G ? want : m->kw.G;
+}
+
+fv_status krylov_setup(fv_mesh *m)
+{
+    KrylovWork &w = m->kw;
+    int per_sm = 0;
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kBlock, 0));
+    int per_sm2 = 0;
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_bicgstab, kBlock, 0));
+    per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
+    FV_CHECK(per_sm >= 1, FV_E_CUDA, "Krylov kernels cannot be resident");
+    w.block = kBlock;
+    w.G = m->sm_count * (per_sm < 2 ? per_sm : 2);
+    const size_t N = m->N;
+    DeviceArena &ar = m->arena;
+    fv_status st;
+    if ((st = ar.alloc_n(&w.val, (size_t)m->nnz)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.val2, (size_t)m->nnz)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.dinv, N)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.r, N)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.p, N)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.q, N)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.y, N)) != FV_OK) return st;
+    for (int k = 0; k < 8; ++k)
+        if ((st = ar.alloc_n(&w.bv[k], 3 * N)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.partials, (size_t)2 * w.G * kParts)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.bar, 1)) != FV_OK) return st;
+    if ((st = ar.alloc_n(&w.stats, 4)) != FV_OK) return st;
+    FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
+    return FV_OK;
+}
+
+fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb)
+{
+    const KrylovWork &w = m->kw;
+    CgArgs a;
+    a.N = m->N;
+    a.slice_ptr = m->slice_ptr;
+    a.col = m->col;
+    a.val = pb.val;
+    a.diag = pb.diag;
+    a.b = pb.b;
+    a.x = pb.x;
+    a.s = w.dinv;
+    a.r = w.r;
+    a.p = w.p;
+    a.q = w.q;
+    a.y = w.y;
+    a.partA = w.partials;
+    a.partB = w.partials + (size_t)w.G * kParts;
+    a.bar = w.bar;
+    a.spin = g_spin_limit;
+    a.tol = pb.tol;
+    a.reltol = pb.reltol;
+    a.maxit = pb.maxit;
+    a.stats = pb.stats;
+    FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
+    void *args[] = {&a};
+    return coop_launch((const void *)k_pcg, grid_for(m, m->N), args, m->stream);
+}
+
+fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)
+{
+    const KrylovWork &w = m->kw;
+    BicgArgs a;
+    a.N = m->N;
+    a.ncomp = pb.ncomp;
+    a.slice_ptr = m->slice_ptr;
+    a.col = m->col;
+    a.val = pb.val;
+    a.diag = pb.diag;
+    a.b = pb.b;
+    a.src = pb.src;
+    a.gradp = pb.gradp;
+    a.V = m->V;
+    a.x = pb.x;
+    a.dinv = w.dinv;
+    a.r = w.bv[0];
+    a.rh = w.bv[1];
+    a.p = w.bv[2];
+    a.v = w.bv[3];
+    a.y = w.bv[4];
+    a.s = w.bv[5];
+    a.z = w.bv[6];
+    a.t = w.bv[7];
+    a.partA = w.partials;
+    a.partB = w.partials + (size_t)w.G * kParts;
+    a.bar = w.bar;
+    a.spin = g_spin_limit;
+    a.tol = pb.tol;
+    a.reltol = pb.reltol;
+    a.maxit = pb.maxit;
+    a.stats = pb.stats;
+    FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
+    void *args[] = {&a};
+    return coop_launch((const void *)k_bicgstab, grid_for(m, m->N), args, m->stream);
+}
+
+}  // namespace fvgb
+
+extern "C" fv_status fv_set_barrier_spin_limit(int64_t limit)
+{
+    FV_CHECK(limit >= 0, FV_E_INVALID, "negative spin limit");
+    fvgb::g_spin_limit = limit > 0 ? limit : (1LL << 25);
+    return FV_OK;
+}

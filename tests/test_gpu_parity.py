@@ -1,0 +1,389 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Bar: mesh addressing bit-exact; FP64 fields within 1e-9 relative L2; Krylov
+iteration counts within +-1 (the tolerance of the FP64 path); plus the
+degenerate cases (one cell, zero right-hand side, iteration limit, barrier
+time-out) and determinism."""
+import numpy as np
+import pytest
+
+import meshgen as mg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1207_1571_gb300 import build as B
+    B.build()
+    import paper_1207_1571_gb300 as P
+    P.load()
+    return P
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def t64(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def both(P, m, nu, renumber=True, precision=0):
+    mesh = P.Mesh(m, renumber=renumber)
+    case = P.Case(mesh, nu, precision)
+    om = O.Mesh(m, renumber=renumber)
+    oc = O.Case(om, nu)
+    return mesh, case, om, oc
+
+
+def assert_fields(case, oc, tol=TOL):
+    u, p, phi = case.get_fields_host()
+    uo, po, phio = oc.get_fields()
+    assert rel(u, uo) <= tol, ("u", rel(u, uo))
+    assert rel(p, po) <= tol, ("p", rel(p, po))
+    assert rel(phi, phio) <= tol, ("phi", rel(phi, phio))
+
+
+def assert_iters(s, so):
+    gi, oi = np.array(s["iters"]), np.array(so["iters"])
+    assert np.abs(gi - oi).max() <= 1, (gi, oi)
+
+
+# ------------------------------------------------------------ addressing --
+
+@pytest.mark.parametrize("maker", [
+    lambda: mg.permute_cells(mg.cavity3d(10), mg.random_permutation(1000, 1234)),
+    lambda: mg.tet_box(3, 3, 5, jitter=0.1),
+    lambda: mg.cavity2d(20)])
+def test_mesh_addressing_bit_exact(P, maker):
+    m = maker()
+    mesh = P.Mesh(m, renumber=True)
+    om = O.Mesh(m, renumber=True)
+    c, f, fl = om.orders()
+    assert np.array_equal(mesh.cell_order(), c)
+    gf, gfl = mesh.face_order()
+    assert np.array_equal(gf, f) and np.array_equal(gfl, fl)
+    own, nei = mesh.addressing()
+    oown, onei = om.addressing()
+    assert np.array_equal(own.cpu().numpy(), oown) and np.array_equal(nei.cpu().numpy(), onei)
+    assert mesh.info()["nonorth"] == om.nonorth
+
+
+def test_gauss_grad_and_matvec(P):
+    m = mg.tet_box(4, 3, 5, jitter=0.1)
+    mesh = P.Mesh(m, renumber=True)
+    om = O.Mesh(m, renumber=True)
+    rng = np.random.default_rng(0)
+    x, xb = rng.standard_normal(m.n_cells), rng.standard_normal(m.n_boundary_faces)
+    g = mesh.gauss_grad(t64(x), t64(xb)).cpu().numpy()
+    assert rel(g, om.gauss_grad(x, xb)) <= 1e-13
+    own, nei = om.addressing()
+    F = m.n_internal_faces
+    d, up, lo = rng.random(m.n_cells) + 5, rng.standard_normal(F), rng.standard_normal(F)
+    y = mesh.ldu_matvec(t64(d), t64(up), t64(lo), t64(x)).cpu().numpy()
+    assert rel(y, O.ldu_matvec(own, nei, d, up, lo, x)) <= 1e-14
+
+
+# --------------------------------------------------------------- solvers --
+
+def _pressure_system(m, nu, dt, steps, ref):
+    om = O.Mesh(m, renumber=True)
+    oc = O.Case(om, nu)
+    for _ in range(steps):
+        oc.piso_step(dt, 2, p_ref_cell=ref)
+    return om, oc, oc.pressure_system(dt, p_ref_cell=ref)
+
+
+@pytest.mark.parametrize("which", ["2d", "3d", "tet", "3d_big"])
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_pcg_matches_oracle(P, which, tol):
+    if which == "2d":
+        m, nu, dt = mg.cavity2d(20), 0.1, 0.005
+    elif which == "3d":
+        m, nu, dt = mg.permute_cells(mg.cavity3d(12), mg.random_permutation(1728, 7)), 0.01, 0.01
+    elif which == "3d_big":
+        m, nu, dt = mg.cavity3d(24), 0.01, 0.01          # several blocks, grid barrier
+    else:
+        m, nu, dt = mg.tet_box(4, 4, 4, jitter=0.1), 0.05, 0.02
+        m.patches[0].u = (0.5, 0.0, 0.2)
+    om, oc, (d, up, b) = _pressure_system(m, nu, dt, 2, m.corner_cell)
+    own, nei = om.addressing()
+    x0 = np.random.default_rng(1).standard_normal(m.n_cells) * 1e-3
+    xo, ito, r0o, r1o, sto = O.pcg(own, nei, d, up, b, x0, tol=tol)
+    mesh = P.Mesh(m, renumber=True)
+    x = t64(x0)
+    s = mesh.pcg_solve(t64(d), t64(up), t64(b), x, tol=tol)
+    assert s["status"] == 0 and sto == 0
+    assert abs(s["iters"] - ito) <= 1, (s["iters"], ito)
+    assert rel(x.cpu().numpy(), xo) <= TOL
+    assert s["res"] <= tol and abs(s["res0"] - r0o) <= 1e-12 * r0o
+
+
+def test_pcg_degenerate_cases(P):
+    m = mg.cavity3d(6)
+    om, oc, (d, up, b) = _pressure_system(m, 0.01, 0.02, 1, 0)
+    mesh = P.Mesh(m, renumber=True)
+    # zero right-hand side: x = 0 without iterating
+    x = t64(np.ones(m.n_cells))
+    s = mesh.pcg_solve(t64(d), t64(up), t64(0 * b), x)
+    assert s["iters"] == 0 and s["status"] == 0 and not x.cpu().numpy().any()
+    # exact start: no iteration
+    own, nei = om.addressing()
+    xs = O.pcg(own, nei, d, up, b, np.zeros(m.n_cells), tol=1e-14)[0]
+    x = t64(xs)
+    s = mesh.pcg_solve(t64(d), t64(up), t64(b), x, tol=1e-8)
+    assert s["iters"] == 0
+    # iteration limit reached: status NOT_CONVERGED, same iterate as the oracle
+    x = t64(np.zeros(m.n_cells))
+    s = mesh.pcg_solve(t64(d), t64(up), t64(b), x, tol=1e-12, maxit=5)
+    xo, ito, _, _, sto = O.pcg(own, nei, d, up, b, np.zeros(m.n_cells), tol=1e-12, maxit=5)
+    assert s["status"] == 4 and sto == -1 and s["iters"] == ito == 5
+    assert rel(x.cpu().numpy(), xo) <= TOL
+
+
+@pytest.mark.parametrize("which", ["2d", "tet"])
+def test_bicgstab_matches_oracle(P, which):
+    if which == "2d":
+        m, nu, dt = mg.cavity2d(16), 0.02, 0.05
+    else:
+        m, nu, dt = mg.tet_box(3, 3, 3, jitter=0.1), 0.02, 0.05
+        m.patches[0].u = (1.0, 0.0, 0.5)
+    om = O.Mesh(m, renumber=True)
+    oc = O.Case(om, nu)
+    for _ in range(3):
+        oc.piso_step(dt, 2, p_ref_cell=m.corner_cell)
+    d, up, lo, src = oc.momentum_system(True, dt)
+    own, nei = om.addressing()
+    x0 = np.zeros(m.n_cells)
+    for tol in (1e-6, 1e-12):
+        xo, ito, r0o, r1o, sto = O.bicgstab(own, nei, d, up, lo, src[0], x0, tol=tol)
+        mesh = P.Mesh(m, renumber=True)
+        x = t64(x0)
+        s = mesh.bicgstab_solve(t64(d), t64(up), t64(lo), t64(src[0]), x, tol=tol)
+        assert s["status"] == 0 and abs(s["iters"] - ito) <= 1, (s, ito)
+        assert rel(x.cpu().numpy(), xo) <= TOL
+
+
+# -------------------------------------------------------------- PISO step --
+
+def test_piso_2d_cavity_100_steps(P):
+    """The 2-D lid-driven cavity workload: 20x20, nu 0.1, dt 0.005, 100 steps,
+    2 correctors, CG to 1e-6."""
+    m = mg.cavity2d(20)
+    mesh, case, om, oc = both(P, m, 0.1)
+    for step in range(100):
+        s = case.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
+        so = oc.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
+        assert s["status"] == 0
+        assert_iters(s, so)
+    assert_fields(case, oc)
+    u, p, phi = case.get_fields_host()
+    assert np.abs(u[2]).max() == 0.0
+
+
+def test_piso_3d_cavity_permuted(P):
+    n = 14
+    m = mg.permute_cells(mg.cavity3d(n), mg.random_permutation(n ** 3, 1234))
+    mesh, case, om, oc = both(P, m, 0.01)
+    for step in range(8):
+        s = case.piso_step(0.01, 2, p_ref_cell=m.corner_cell)
+        so = oc.piso_step(0.01, 2, p_ref_cell=m.corner_cell)
+        assert s["status"] == 0
+        assert_iters(s, so)
+    assert_fields(case, oc)
+
+
+def test_piso_tets_nonorthogonal(P):
+    m = mg.tet_box(4, 4, 4, jitter=0.1)
+    m.patches[0].u = (1.0, 0.0, 0.0)
+    mesh, case, om, oc = both(P, m, 0.05)
+    assert mesh.info()["nonorth"]
+    for step in range(5):
+        s = case.piso_step(0.01, 2, p_ref_cell=0)
+        so = oc.piso_step(0.01, 2, p_ref_cell=0)
+        assert_iters(s, so)
+    assert_fields(case, oc)
+
+
+def test_piso_time_dependent_boundary_values(P):
+    """Taylor-Green-like walls whose face values change every step."""
+    n = 12
+    L = np.pi
+    sp = {"xmin": "walls", "xmax": "walls", "ymin": "walls", "ymax": "walls",
+          "zmin": "fb", "zmax": "fb"}
+    specs = {"walls": (mg.WALL, (0, 0, 0), 0.0), "fb": (mg.EMPTY, (0, 0, 0), 0.0)}
+    m = mg.permute_cells(mg.hex_box(n, n, 1, (L, L, L / n), sp, specs),
+                         mg.random_permutation(n * n, 5))
+    mesh, case, om, oc = both(P, m, 0.01)
+    F = m.n_internal_faces
+    w = m.patches[0]
+    Cw = m.Cf[:, F + w.start:F + w.start + w.size]
+    u0 = np.stack([np.sin(m.C[0]) * np.cos(m.C[1]), -np.cos(m.C[0]) * np.sin(m.C[1]), 0 * m.C[0]])
+    case.set_fields_host(u0, np.zeros(m.n_cells), np.zeros(m.n_faces))
+    oc.set_fields(u0, np.zeros(m.n_cells), np.zeros(m.n_faces))
+    for k in range(6):
+        t = 0.05 * (k + 1)
+        f = np.exp(-0.02 * t)
+        ub = np.stack([np.sin(Cw[0]) * np.cos(Cw[1]) * f, -np.cos(Cw[0]) * np.sin(Cw[1]) * f,
+                       0 * Cw[0]])
+        case.set_patch_faces(0, ub)
+        oc.set_patch_faces(0, ub)
+        s = case.piso_step(0.05, 2, p_ref_cell=0)
+        so = oc.piso_step(0.05, 2, p_ref_cell=0)
+        assert_iters(s, so)
+    assert_fields(case, oc)
+
+
+def test_piso_single_cell(P):
+    m = mg.cavity3d(1)
+    mesh, case, om, oc = both(P, m, 0.01)
+    for _ in range(3):
+        s = case.piso_step(0.01, 2, p_ref_cell=0)
+        so = oc.piso_step(0.01, 2, p_ref_cell=0)
+        assert_iters(s, so)
+    assert_fields(case, oc, tol=1e-12)
+
+
+def test_piso_iteration_limit_status(P):
+    m = mg.cavity2d(12)
+    mesh, case, om, oc = both(P, m, 0.1)
+    s = case.piso_step(0.005, 2, p_ref_cell=0, p_maxit=4)
+    so = oc.piso_step(0.005, 2, p_ref_cell=0, p_maxit=4)
+    assert s["status"] == 4 and s["p"][0]["status"] == 4
+    assert so["status"] == -1
+    assert_iters(s, so)
+    assert_fields(case, oc)
+
+
+def test_graph_replay_and_determinism(P):
+    m = mg.permute_cells(mg.cavity3d(10), mg.random_permutation(1000, 2))
+    mesh = P.Mesh(m, renumber=True)
+    a, b = P.Case(mesh, 0.01), P.Case(mesh, 0.01)
+    for _ in range(4):
+        a.piso_step(0.01, 2, p_ref_cell=m.corner_cell)
+    sb = b.run_graph(4, 0.01, 2, p_ref_cell=m.corner_cell)
+    ua, pa, fa = a.get_fields_host()
+    ub, pb, fb = b.get_fields_host()
+    # same kernels, same order, fixed reduction order: identical bits
+    assert np.array_equal(ua, ub) and np.array_equal(pa, pb) and np.array_equal(fa, fb)
+    assert sb["status"] == 0
+
+
+def test_fields_roundtrip(P):
+    m = mg.permute_cells(mg.cavity3d(5), mg.random_permutation(125, 9))
+    mesh = P.Mesh(m, renumber=True)
+    case = P.Case(mesh, 0.01)
+    rng = np.random.default_rng(3)
+    u, p, phi = rng.standard_normal((3, 125)), rng.standard_normal(125), rng.standard_normal(m.n_faces)
+    case.set_fields(t64(u), t64(p), t64(phi))
+    gu, gp, gphi = case.get_fields()
+    assert np.array_equal(gu.cpu().numpy(), u) and np.array_equal(gp.cpu().numpy(), p)
+    assert np.array_equal(gphi.cpu().numpy(), phi)
+    hu, hp, hphi = case.get_fields_host()
+    assert np.array_equal(hu, u) and np.array_equal(hphi, phi)
+    # internal order equals the oracle's internal order
+    om = O.Mesh(m, renumber=True); oc = O.Case(om, 0.01); oc.set_fields(u, p, phi)
+    iu, ip, iphi = case.get_fields(original_order=False)
+    ou, op, ophi = oc.state()
+    assert np.array_equal(iu.cpu().numpy(), ou) and np.array_equal(iphi.cpu().numpy(), ophi)
+
+
+# ------------------------------------------------------------ SIMPLE step --
+
+def test_simple_channel_outlet(P):
+    m = mg.channel2d(24, 8, 2.0, 1.0)
+    mesh, case, om, oc = both(P, m, 0.1)
+    F = m.n_internal_faces
+    inl = m.patches[m.patch("inlet")]
+    y = m.Cf[1, F + inl.start:F + inl.start + inl.size]
+    prof = np.stack([6 * y * (1 - y), 0 * y, 0 * y])
+    case.set_patch_faces(m.patch("inlet"), prof)
+    oc.set_patch_faces(m.patch("inlet"), prof)
+    for it in range(30):
+        s = case.simple_iter(0.7, 0.3)
+        so = oc.simple_iter(0.7, 0.3)
+        assert_iters(s, so)
+        assert abs(s["init_res_max"] - so["init_res_max"]) <= 1e-8 * max(so["init_res_max"], 1e-300) \
+            or so["init_res_max"] < 1e-12
+    assert_fields(case, oc)
+
+
+def test_simple_duct_tets(P):
+    m = mg.duct_tets(4, 8)
+    mesh, case, om, oc = both(P, m, 0.05)
+    F = m.n_internal_faces
+    inl = m.patches[m.patch("inlet")]
+    xy = m.Cf[:2, F + inl.start:F + inl.start + inl.size]
+    prof = mg.duct_inlet_profile(xy)
+    ub = np.stack([0 * prof, 0 * prof, prof])
+    case.set_patch_faces(m.patch("inlet"), ub)
+    oc.set_patch_faces(m.patch("inlet"), ub)
+    for it in range(10):
+        s = case.simple_iter(0.7, 0.3)
+        so = oc.simple_iter(0.7, 0.3)
+        assert_iters(s, so)
+    assert_fields(case, oc)
+    assert s["init_res_max"] == pytest.approx(so["init_res_max"], rel=1e-7)
+
+
+# --------------------------------------------------------- failure paths --
+
+def test_barrier_timeout_is_reported(P):
+    """A device-side wait that runs out returns FV_E_TIMEOUT; the context
+    stays usable.  The wait limit is shrunk on the host to force it."""
+    from paper_1207_1571_gb300 import _capi
+    m = mg.cavity3d(40)
+    om, oc, (d, up, b) = _pressure_system(m, 0.01, 0.01, 1, 0)
+    mesh = P.Mesh(m, renumber=True)
+    L = P.load()
+    assert L.fv_set_barrier_spin_limit(1) == 0
+    try:
+        x = t64(np.zeros(m.n_cells))
+        import ctypes as C
+        prm = _capi.fv_pcg_params(1e-6, 0.0, 10000, 0)
+        st = _capi.fv_solve_stats()
+        rc = L.fv_pcg_solve(mesh.h, t64(d).data_ptr(), t64(up).data_ptr(), t64(b).data_ptr(),
+                            x.data_ptr(), C.byref(prm), C.byref(st))
+        assert rc == 6 and st.status == 6
+    finally:
+        L.fv_set_barrier_spin_limit(0)
+    x = t64(np.zeros(m.n_cells))
+    s = mesh.pcg_solve(t64(d), t64(up), t64(b), x)
+    assert s["status"] == 0
+
+
+def test_closed_domain_needs_reference(P):
+    m = mg.cavity2d(4)
+    mesh = P.Mesh(m)
+    case = P.Case(mesh, 0.1)
+    with pytest.raises(P.FvError) as e:
+        case.piso_step(0.01, 2, p_ref_cell=-1)
+    assert e.value.status == 1
+
+
+# --------------------------------------------------- full-size workload --
+
+def test_full_size_cavity_100_cubed_first_step(P):
+    """The 1M-cell cavity (100^3, permuted with seed 1234, RCM), one PISO step
+    from rest at the launch configuration of the benchmark, against the
+    oracle (about half a minute of CPU)."""
+    n = 100
+    m = mg.permute_cells(mg.cavity3d(n), mg.random_permutation(n ** 3, 1234))
+    mesh, case, om, oc = both(P, m, 0.01)
+    assert np.array_equal(mesh.cell_order(), om.orders()[0])
+    s = case.piso_step(0.002, 2, p_ref_cell=m.corner_cell)
+    so = oc.piso_step(0.002, 2, p_ref_cell=m.corner_cell)
+    assert s["status"] == 0
+    assert_iters(s, so)
+    assert_fields(case, oc)
