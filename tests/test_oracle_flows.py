@@ -63,6 +63,32 @@ def test_simple_continuity_identity_tets():
         assert st["status"] == 0 and st["cont_err"] < 1e-12
 
 
+def test_cavity2d_cg_stop_is_rounding_sensitive_late():
+    """Property of the 2-D cavity workload (20x20, nu 0.1, dt 0.005, CG to
+    1e-6) that bounds any parity claim: its pressure-CG residual is not
+    monotone, and from about step 83 on it dips to the threshold and climbs
+    again inside a solve.  A 1e-16 perturbation of the initial velocity then
+    changes the oracle's own iteration counts by more than one and its final
+    pressure by far more than 1e-9, while the first 80 steps are unaffected."""
+    m = mg.cavity2d(20)
+
+    def run(eps, seed):
+        oc = O.Case(O.Mesh(m, renumber=True), 0.1)
+        u = np.zeros((3, m.n_cells))
+        u[:2] = eps * np.random.default_rng(seed).standard_normal((2, m.n_cells))
+        oc.set_fields(u, np.zeros(m.n_cells), np.zeros(m.n_faces))
+        its = [oc.piso_step(0.005, 2, p_ref_cell=m.corner_cell)["iters"][3:].copy()
+               for _ in range(100)]
+        return np.array(its), oc.get_fields()[1]
+
+    base, p0 = run(0.0, 0)
+    pert, p1 = run(1e-16, 0)
+    diff = np.abs(base - pert).max(axis=1)
+    assert diff[1:80].max() <= 1
+    assert diff[80:].max() > 1
+    assert np.linalg.norm(p1 - p0) > 1e-6 * np.linalg.norm(p0)
+
+
 # ---------------------------------------------------------------------------
 # plane Couette flow: u = U y/H is reproduced to rounding
 # ---------------------------------------------------------------------------
