@@ -75,6 +75,21 @@ def cg_bytes_per_iter(N, F):
     return 104 * N + 16 * F
 
 
+def cg_flops_per_iter(N, F):
+    """Algorithmic FP64 flops of one Jacobi-PCG iteration: SMVP 2(N + 2F),
+    p.q 2N, two axpys 4N, z = r/d N, r.z 2N, p update 2N, ||r||^2 2N."""
+    return 15 * N + 4 * F
+
+
+def fp64_peak_tflops(dev, sm_mhz):
+    """FP64 peak from unit counts and clock: GB300 issues 2 FP64 FMA per
+    clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+    peak_sustained = 2 per cycle per SM)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return 2 * 2 * sms * sm_mhz * 1e6 / 1e12
+
+
 class Clocks:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
@@ -201,7 +216,7 @@ def run_ours(args, ws, rank, local):
           for _ in range(args.steps)]
     L.fv_profile_read(None, None, 1)
     L.fv_profile_enable(1)
-    iters_p, iters_u, statuses = 0, 0, []
+    iters_p, iters_u, statuses, per_solve = 0, 0, [], []
     barrier(ws)
     torch.cuda.synchronize()
     with Clocks(dev) as clk:
@@ -216,6 +231,7 @@ def run_ours(args, ws, rank, local):
             stats = case.last_stats()
             iters_p += sum(stats["iters"][3:])
             iters_u += sum(stats["iters"][:3])
+            per_solve.extend(stats["iters"][3:])
             statuses.append(stats["status"])
         torch.cuda.synchronize()
     barrier(ws)
@@ -232,8 +248,15 @@ def run_ours(args, ws, rank, local):
     peak, peak_kind = peaks()
     achieved = bpi * iters_p / pcg_s / 1e9 if pcg_s > 0 else None
     traffic = None
+    n_solves = max(1, len(per_solve))
     if PCG_TRAFFIC["source_sha1"] == source_sha1() and PCG_TRAFFIC["bytes_per_iter"]:
-        traffic = PCG_TRAFFIC["bytes_per_iter"] * iters_p / args.steps / (2 * 1.0)
+        # per launch = per-iteration DRAM bytes x mean iterations per launch
+        traffic = PCG_TRAFFIC["bytes_per_iter"] * iters_p / n_solves
+    clk_sum = clk.summary()
+    sm_mhz = clk_sum.get("sm_mhz") or 2070.0
+    fp64_peak = fp64_peak_tflops(dev, sm_mhz)
+    flops = cg_flops_per_iter(N, F) * iters_p
+    fp64_achieved = flops / pcg_s / 1e12 if pcg_s > 0 else None
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -267,6 +290,8 @@ def run_ours(args, ws, rank, local):
                    "l2": "flushed (256 MiB write) between timed steps; steps timed from rest",
                    "parallelism": "replicas only" if ws > 1 else "1 GPU"},
         "cg": {"iterations": iters_p, "iters_per_step": iters_p / args.steps,
+               "per_solve": per_solve,
+               "us_per_iter": 1e3 * prof_ms[4] / iters_p if iters_p else None,
                "bicgstab_iterations": iters_u, "ms": prof_ms[4],
                "share_of_step": prof_ms[4] / (1e3 * t_local) if t_local > 0 else None},
         "stages_ms": {n: prof_ms[k] for k, n in enumerate(_capi.PROF_STAGES)},
@@ -274,8 +299,13 @@ def run_ours(args, ws, rank, local):
                      "unit": "GB/s", "frac": achieved / peak if achieved else None,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "bytes_per_iter": bpi, "algorithmic": "104N+16F bytes per CG iteration"},
+        "roofline_fp64": {"bound": "alu", "kernel": "k_pcg", "achieved": fp64_achieved,
+                          "peak": fp64_peak, "unit": "TFLOP/s",
+                          "frac": fp64_achieved / fp64_peak if fp64_achieved else None,
+                          "peak_kind": "derived: 2 FP64 FMA/clk/SM x SMs x median SM clock x 2",
+                          "algorithmic": "15N+4F flops per CG iteration"},
         "gpu_launches": int(sum(prof_n[k] for k in range(7))),
-        "clocks": clk.summary(),
+        "clocks": clk_sum,
         "e2e": e2e,
         "memory_bytes": case.memory_bytes(),
         "statuses": sorted(set(statuses)),

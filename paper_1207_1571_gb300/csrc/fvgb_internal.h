@@ -86,7 +86,8 @@ struct GridBar {
 
 // Persistent Krylov workspace, sized for one mesh.
 struct KrylovWork {
-    int G = 0;               // cooperative grid size used for this mesh
+    int G = 0;               // cooperative grid size of the BiCGStab kernel
+    int Gcg = 0;             // cooperative grid size of the CG kernel (one block per SM)
     int block = 0;
     double *val = nullptr;   // SELL values (scaled copy for CG)
     double *val2 = nullptr;  // second SELL value buffer (BiCGStab input copy)

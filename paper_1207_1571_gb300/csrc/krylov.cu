@@ -139,6 +139,75 @@ __device__ bool grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &
 }
 
 // ------------------------------------------------------------------ CG --
+//
+// One block of kCgBlock threads per SM; block b owns the contiguous rows
+// [b*chunk, (b+1)*chunk) (whole 32-row slices) for the whole solve, so the
+// neighbour gathers of a block mostly hit its own SM's L1.  Gathers are
+// plain loads: the grid barrier's acquire orders them after the writes of
+// the previous phase.
+//
+// Reductions keep FP64 work low (GB300 runs FP64 at about 2 FMA per clock
+// per SM): threads drop their partial sums into shared memory and one warp
+// adds them in a fixed order; after the grid barrier one warp adds the
+// per-block partials, again in a fixed order.
+
+constexpr int kCgBlock = 1024;
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int NV>
+__device__ __forceinline__ void cg_block_sum(double (&v)[NV], double (*buf)[kCgBlock])
+{
+#pragma unroll
+    for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = 0.0;
+#pragma unroll 8
+            for (int j = 0; j < kCgBlock / 32; ++j) x += buf[k][threadIdx.x + 32 * j];
+            x = warp_sum(x);
+            if (threadIdx.x == 0) buf[k][0] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = buf[k][0];
+    __syncthreads();
+}
+
+template <int NV>
+__device__ bool cg_grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &gen,
+                            long long limit, double (*buf)[kCgBlock])
+{
+    cg_block_sum<NV>(v, buf);
+    if (gridDim.x == 1) return true;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[blockIdx.x * kParts + k] = v[k];
+    }
+    if (!grid_sync(bar, gen, limit)) return false;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = 0.0;
+            for (int j = threadIdx.x; j < (int)gridDim.x; j += 32) x += __ldcg(part + j * kParts + k);
+            x = warp_sum(x);
+            if (threadIdx.x == 0) buf[k][0] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = buf[k][0];
+    __syncthreads();
+    return true;
+}
 
 struct CgArgs {
     int N;
@@ -154,18 +223,22 @@ struct CgArgs {
     DevSolveStats *stats;
 };
 
-__global__ void __launch_bounds__(kBlock, 2) k_pcg(CgArgs a)
+__global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
 {
+    __shared__ double buf[3][kCgBlock];
     const int N = a.N;
-    const int stride = gridDim.x * kBlock;
-    const int i0 = blockIdx.x * kBlock + threadIdx.x;
+    const int nsl = (N + 31) >> 5;
+    const int chunk = ((nsl + gridDim.x - 1) / gridDim.x) * 32;
+    const int rb = blockIdx.x * chunk;
+    const int re = min(N, rb + chunk);
+    const int i0 = rb + threadIdx.x;
     unsigned gen = 0;
     bool ok = true;
     int status = FV_OK, it = 0;
     double nb = 0.0, nr0 = 0.0, nr = 0.0;
 
     // S1: scaling s = D^-1/2 and scaled start y = D^1/2 x
-    for (int i = i0; i < N; i += stride) {
+    for (int i = i0; i < re; i += kCgBlock) {
         const double d = a.diag[i];
         const double sq = sqrt(d);
         a.s[i] = 1.0 / sq;
@@ -175,7 +248,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg(CgArgs a)
     // S2: scale the off-diagonals, r^ = s (b - A x), norms
     double v3[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||r||^2, r^.r^
     if (ok) {
-        for (int i = i0; i < N; i += stride) {
+        for (int i = i0; i < re; i += kCgBlock) {
             const RowSpan rs = row_span(a.slice_ptr, i);
             const double si = a.s[i], d = a.diag[i], xi = a.x[i];
             double ax = d * xi;
@@ -183,8 +256,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg(CgArgs a)
                 const int e = rs.e0 + 32 * k;
                 const int c = a.col[e];
                 const double v = a.val[e];
-                ax += v * __ldcg(a.x + c);
-                a.val[e] = v * si * __ldcg(a.s + c);
+                ax += v * a.x[c];
+                a.val[e] = v * si * a.s[c];
             }
             const double bi = a.b[i];
             const double rh = si * (bi - ax);
@@ -193,7 +266,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg(CgArgs a)
             v3[1] += d * rh * rh;
             v3[2] += rh * rh;
         }
-        ok = grid_sum<3>(v3, a.partB, a.bar, gen, a.spin);
+        ok = cg_grid_sum<3>(v3, a.partB, a.bar, gen, a.spin, buf);
     }
     double thresh = 0.0, rho = v3[2];
     if (ok) {
@@ -203,65 +276,61 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg(CgArgs a)
         thresh = fmax(a.tol * nb, a.reltol * nr0);
     }
     if (ok && nb == 0.0) {
-        for (int i = i0; i < N; i += stride) a.x[i] = 0.0;
+        for (int i = i0; i < re; i += kCgBlock) a.x[i] = 0.0;
         nr0 = nr = 0.0;
     } else if (ok && nr0 > thresh) {
         double alpha = 0.0, beta = 0.0;
-        bool done = false;
-        while (!done) {
+        while (true) {
             ++it;
             // P1: p = r^ + beta p (first: p = r^); y += alpha_prev p_prev
-            for (int i = i0; i < N; i += stride) {
-                const double ri = a.r[i];
-                if (it == 1) {
-                    a.p[i] = ri;
-                } else {
+            if (it == 1) {
+                for (int i = i0; i < re; i += kCgBlock) a.p[i] = a.r[i];
+            } else {
+                for (int i = i0; i < re; i += kCgBlock) {
                     const double po = a.p[i];
                     a.y[i] += alpha * po;
-                    a.p[i] = ri + beta * po;
+                    a.p[i] = a.r[i] + beta * po;
                 }
             }
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
             // P2: q = A^ p (unit diagonal), p.q
             double v1[1] = {0.0};
-            for (int i = i0; i < N; i += stride) {
+            for (int i = i0; i < re; i += kCgBlock) {
                 const RowSpan rs = row_span(a.slice_ptr, i);
                 const double pi = a.p[i];
                 double acc = pi;
                 for (int k = 0; k < rs.K; ++k) {
                     const int e = rs.e0 + 32 * k;
-                    acc += a.val[e] * __ldcg(a.p + a.col[e]);
+                    acc += a.val[e] * a.p[a.col[e]];
                 }
                 a.q[i] = acc;
                 v1[0] += pi * acc;
             }
-            if (!(ok = grid_sum<1>(v1, a.partA, a.bar, gen, a.spin))) break;
+            if (!(ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf))) break;
             const double pq = v1[0];
             if (!(pq > 0.0) || !isfinite(pq)) { status = FV_E_DIVERGED; alpha = 0.0; break; }
             alpha = rho / pq;
             // P3: r^ -= alpha q; r^.r^ and ||D^1/2 r^||^2
             double v2[2] = {0.0, 0.0};
-            for (int i = i0; i < N; i += stride) {
+            for (int i = i0; i < re; i += kCgBlock) {
                 const double ri = a.r[i] - alpha * a.q[i];
                 a.r[i] = ri;
-                v2[0] += ri * ri;
-                v2[1] += a.diag[i] * ri * ri;
+                const double r2 = ri * ri;
+                v2[0] += r2;
+                v2[1] += a.diag[i] * r2;
             }
-            if (!(ok = grid_sum<2>(v2, a.partB, a.bar, gen, a.spin))) break;
+            if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf))) break;
             nr = sqrt(v2[1]);
             if (!isfinite(nr)) { status = FV_E_DIVERGED; break; }
-            if (nr <= thresh) { done = true; break; }
-            if (it >= a.maxit) { status = FV_E_NOT_CONVERGED; done = true; break; }
+            if (nr <= thresh) break;
+            if (it >= a.maxit) { status = FV_E_NOT_CONVERGED; break; }
             beta = v2[0] / rho;
             rho = v2[0];
         }
         if (ok) {
             // final update of the scaled iterate, then x = D^-1/2 y
             const double af = (status == FV_E_DIVERGED) ? 0.0 : alpha;
-            for (int i = i0; i < N; i += stride) {
-                const double yi = a.y[i] + af * a.p[i];
-                a.x[i] = a.s[i] * yi;
-            }
+            for (int i = i0; i < re; i += kCgBlock) a.x[i] = a.s[i] * (a.y[i] + af * a.p[i]);
         }
     }
     if (!ok) status = FV_E_TIMEOUT;
@@ -446,11 +515,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
 
 // ------------------------------------------------------------ launches --
 
-static fv_status coop_launch(const void *fn, int G, void **args, cudaStream_t s)
+static fv_status coop_launch(const void *fn, int G, int block, void **args, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(kBlock);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -462,26 +531,27 @@ static fv_status coop_launch(const void *fn, int G, void **args, cudaStream_t s)
     return FV_OK;
 }
 
-static int grid_for(const fv_mesh *m, int rows)
+static int grid_for(int rows, int block, int gmax)
 {
     // about 4 rows per thread at least before another block is worth a
     // grid-wide barrier; never more blocks than can be co-resident
-    int want = (rows + 4 * kBlock - 1) / (4 * kBlock);
+    int want = (rows + 4 * block - 1) / (4 * block);
     if (want < 1) want = 1;
-    return want < m->kw.G ? want : m->kw.G;
+    return want < gmax ? want : gmax;
 }
 
 fv_status krylov_setup(fv_mesh *m)
 {
     KrylovWork &w = m->kw;
     int per_sm = 0;
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kBlock, 0));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kCgBlock, 0));
+    FV_CHECK(per_sm >= 1, FV_E_CUDA, "CG kernel cannot be resident");
+    w.Gcg = m->sm_count;
     int per_sm2 = 0;
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_bicgstab, kBlock, 0));
-    per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
-    FV_CHECK(per_sm >= 1, FV_E_CUDA, "Krylov kernels cannot be resident");
+    FV_CHECK(per_sm2 >= 1, FV_E_CUDA, "BiCGStab kernel cannot be resident");
     w.block = kBlock;
-    w.G = m->sm_count * (per_sm < 2 ? per_sm : 2);
+    w.G = m->sm_count * (per_sm2 < 2 ? per_sm2 : 2);
     const size_t N = m->N;
     DeviceArena &ar = m->arena;
     fv_status st;
@@ -494,7 +564,8 @@ fv_status krylov_setup(fv_mesh *m)
     if ((st = ar.alloc_n(&w.y, N)) != FV_OK) return st;
     for (int k = 0; k < 8; ++k)
         if ((st = ar.alloc_n(&w.bv[k], 3 * N)) != FV_OK) return st;
-    if ((st = ar.alloc_n(&w.partials, (size_t)2 * w.G * kParts)) != FV_OK) return st;
+    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
+    if ((st = ar.alloc_n(&w.partials, (size_t)2 * gp * kParts)) != FV_OK) return st;
     if ((st = ar.alloc_n(&w.bar, 1)) != FV_OK) return st;
     if ((st = ar.alloc_n(&w.stats, 4)) != FV_OK) return st;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
@@ -517,8 +588,9 @@ fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb)
     a.p = w.p;
     a.q = w.q;
     a.y = w.y;
+    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
     a.partA = w.partials;
-    a.partB = w.partials + (size_t)w.G * kParts;
+    a.partB = w.partials + (size_t)gp * kParts;
     a.bar = w.bar;
     a.spin = g_spin_limit;
     a.tol = pb.tol;
@@ -527,7 +599,8 @@ fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb)
     a.stats = pb.stats;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
     void *args[] = {&a};
-    return coop_launch((const void *)k_pcg, grid_for(m, m->N), args, m->stream);
+    return coop_launch((const void *)k_pcg, grid_for(m->N, kCgBlock, w.Gcg), kCgBlock, args,
+                       m->stream);
 }
 
 fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)
@@ -554,8 +627,9 @@ fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)
     a.s = w.bv[5];
     a.z = w.bv[6];
     a.t = w.bv[7];
+    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
     a.partA = w.partials;
-    a.partB = w.partials + (size_t)w.G * kParts;
+    a.partB = w.partials + (size_t)gp * kParts;
     a.bar = w.bar;
     a.spin = g_spin_limit;
     a.tol = pb.tol;
@@ -564,7 +638,8 @@ fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)
     a.stats = pb.stats;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
     void *args[] = {&a};
-    return coop_launch((const void *)k_bicgstab, grid_for(m, m->N), args, m->stream);
+    return coop_launch((const void *)k_bicgstab, grid_for(m->N, kBlock, w.G), kBlock, args,
+                       m->stream);
 }
 
 }  // namespace fvgb
