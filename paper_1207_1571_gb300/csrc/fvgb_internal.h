@@ -195,6 +195,8 @@ struct CgProblem {
 };
 fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb);
 
+
+
 struct BicgProblem {
     const double *diag;      // [N]
     const double *val;       // SELL off-diagonals (non-symmetric)

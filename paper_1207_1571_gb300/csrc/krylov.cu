@@ -11,7 +11,8 @@
 // block takes the same decisions (convergence, breakdown) from bit-identical
 // scalars.  Rows are owned by a fixed thread for the whole solve, so a
 // thread only reads other threads' data where the algorithm needs neighbour
-// values (matrix-vector products); those loads bypass L1 (__ldcg).
+// values (matrix-vector products); the barrier's acquire orders those loads
+// after the writes of the previous phase.
 //
 // CG works on the symmetrically scaled system  D^-1/2 A D^-1/2 y = D^-1/2 b
 // with x = D^-1/2 y: in exact arithmetic this generates the same iterates,
@@ -152,6 +153,7 @@ __device__ bool grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &
 // per-block partials, again in a fixed order.
 
 constexpr int kCgBlock = 1024;
+constexpr int kRedWarps = 4;        // one reducing warp per SM sub-partition
 
 __device__ __forceinline__ double warp_sum(double x)
 {
@@ -160,51 +162,65 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
+// Block sum of NV values.  Threads store their partials in shared memory;
+// warps 0..3 (one per SM sub-partition, so their FP64 work runs in
+// parallel) each add a quarter of them, then thread 0 adds the four results.
+// The order of every addition is fixed.  On return tot[k] (shared) holds the
+// sums; only thread 0 is guaranteed to have seen them before the trailing
+// __syncthreads of the caller.
 template <int NV>
-__device__ __forceinline__ void cg_block_sum(double (&v)[NV], double (*buf)[kCgBlock])
+__device__ __forceinline__ void cg_block_sum(const double (&v)[NV], double (*buf)[kCgBlock],
+                                             double *tot)
 {
+    __shared__ double quarter[NV][kRedWarps];
 #pragma unroll
     for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x < 32) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < kRedWarps) {
+        constexpr int per = kCgBlock / kRedWarps;      // values per warp
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double x = 0.0;
-#pragma unroll 8
-            for (int j = 0; j < kCgBlock / 32; ++j) x += buf[k][threadIdx.x + 32 * j];
+#pragma unroll
+            for (int j = 0; j < per / 32; ++j) x += buf[k][w * per + lane + 32 * j];
             x = warp_sum(x);
-            if (threadIdx.x == 0) buf[k][0] = x;
+            if (lane == 0) quarter[k][w] = x;
         }
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = buf[k][0];
-    __syncthreads();
+        for (int k = 0; k < NV; ++k) {
+            double x = 0.0;
+#pragma unroll
+            for (int q = 0; q < kRedWarps; ++q) x += quarter[k][q];
+            tot[k] = x;
+        }
+    }
 }
 
+// Grid sum of NV values; on return thread 0 of every block holds the same
+// bits in tot[] (shared).  Returns false (all threads) if the barrier failed.
 template <int NV>
-__device__ bool cg_grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &gen,
-                            long long limit, double (*buf)[kCgBlock])
+__device__ bool cg_grid_sum(const double (&v)[NV], double *part, GridBar *bar, unsigned &gen,
+                            long long limit, double (*buf)[kCgBlock], double *tot)
 {
-    cg_block_sum<NV>(v, buf);
+    cg_block_sum<NV>(v, buf, tot);
     if (gridDim.x == 1) return true;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) part[blockIdx.x * kParts + k] = v[k];
+        for (int k = 0; k < NV; ++k) part[blockIdx.x * kParts + k] = tot[k];
     }
     if (!grid_sync(bar, gen, limit)) return false;
-    if (threadIdx.x < 32) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
-            for (int j = threadIdx.x; j < (int)gridDim.x; j += 32) x += __ldcg(part + j * kParts + k);
-            x = warp_sum(x);
-            if (threadIdx.x == 0) buf[k][0] = x;
-        }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < NV) {
+        // warp k adds quantity k over the blocks
+        double x = 0.0;
+        for (int j = lane; j < (int)gridDim.x; j += 32) x += __ldcg(part + j * kParts + w);
+        x = warp_sum(x);
+        if (lane == 0) tot[w] = x;
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = buf[k][0];
     __syncthreads();
     return true;
 }
@@ -223,9 +239,46 @@ struct CgArgs {
     DevSolveStats *stats;
 };
 
+// Scalar state of a CG solve, kept in shared memory and updated by thread 0
+// only (one FP64 divide or square root costs a warp dozens of cycles per
+// instruction on this part, so no thread repeats it).
+struct CgScalars {
+    double alpha, beta, rho, thresh, nb, nr0, nr;
+    int phase;       // 0 iterate, 1 converged, 2 not converged, 3 diverged, 4 zero rhs
+};
+
+// q = A^ p for one row of the unit-diagonal scaled matrix; all loads of
+// the row are issued before the first product (rows have <= 6 entries on
+// hexahedral and tetrahedral meshes; longer rows take the loop).
+__device__ __forceinline__ double spmv_unit_row(const CgArgs &a, const RowSpan &rs, double pi)
+{
+    double acc = pi;
+    if (rs.K <= 6) {
+        int c[6];
+        double v[6], x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) { c[k] = a.col[rs.e0 + 32 * k]; v[k] = a.val[rs.e0 + 32 * k]; }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) x[k] = a.p[c[k]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) acc += v[k] * x[k];
+    } else {
+        for (int k = 0; k < rs.K; ++k) {
+            const int e = rs.e0 + 32 * k;
+            acc += a.val[e] * a.p[a.col[e]];
+        }
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
 {
     __shared__ double buf[3][kCgBlock];
+    __shared__ double tot[3];
+    __shared__ CgScalars sc;
     const int N = a.N;
     const int nsl = (N + 31) >> 5;
     const int chunk = ((nsl + gridDim.x - 1) / gridDim.x) * 32;
@@ -234,8 +287,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
     const int i0 = rb + threadIdx.x;
     unsigned gen = 0;
     bool ok = true;
-    int status = FV_OK, it = 0;
-    double nb = 0.0, nr0 = 0.0, nr = 0.0;
+    int it = 0;
 
     // S1: scaling s = D^-1/2 and scaled start y = D^1/2 x
     for (int i = i0; i < re; i += kCgBlock) {
@@ -246,8 +298,8 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
     }
     ok = grid_sync(a.bar, gen, a.spin);
     // S2: scale the off-diagonals, r^ = s (b - A x), norms
-    double v3[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||r||^2, r^.r^
     if (ok) {
+        double v3[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||r||^2, r^.r^
         for (int i = i0; i < re; i += kCgBlock) {
             const RowSpan rs = row_span(a.slice_ptr, i);
             const double si = a.s[i], d = a.diag[i], xi = a.x[i];
@@ -266,26 +318,29 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             v3[1] += d * rh * rh;
             v3[2] += rh * rh;
         }
-        ok = cg_grid_sum<3>(v3, a.partB, a.bar, gen, a.spin, buf);
+        ok = cg_grid_sum<3>(v3, a.partB, a.bar, gen, a.spin, buf, tot);
     }
-    double thresh = 0.0, rho = v3[2];
-    if (ok) {
-        nb = sqrt(v3[0]);
-        nr0 = sqrt(v3[1]);
-        nr = nr0;
-        thresh = fmax(a.tol * nb, a.reltol * nr0);
+    if (threadIdx.x == 0) {
+        sc.nb = sqrt(tot[0]);
+        sc.nr0 = sqrt(tot[1]);
+        sc.nr = sc.nr0;
+        sc.rho = tot[2];
+        sc.thresh = fmax(a.tol * sc.nb, a.reltol * sc.nr0);
+        sc.alpha = sc.beta = 0.0;
+        sc.phase = sc.nb == 0.0 ? 4 : (sc.nr0 <= sc.thresh ? 1 : 0);
     }
-    if (ok && nb == 0.0) {
+    __syncthreads();
+    if (ok && sc.phase == 4) {
         for (int i = i0; i < re; i += kCgBlock) a.x[i] = 0.0;
-        nr0 = nr = 0.0;
-    } else if (ok && nr0 > thresh) {
-        double alpha = 0.0, beta = 0.0;
+    } else if (ok && sc.phase == 0) {
         while (true) {
             ++it;
             // P1: p = r^ + beta p (first: p = r^); y += alpha_prev p_prev
             if (it == 1) {
                 for (int i = i0; i < re; i += kCgBlock) a.p[i] = a.r[i];
             } else {
+                const double alpha = sc.alpha, beta = sc.beta;
+#pragma unroll 2
                 for (int i = i0; i < re; i += kCgBlock) {
                     const double po = a.p[i];
                     a.y[i] += alpha * po;
@@ -295,23 +350,26 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
             // P2: q = A^ p (unit diagonal), p.q
             double v1[1] = {0.0};
+#pragma unroll 2
             for (int i = i0; i < re; i += kCgBlock) {
                 const RowSpan rs = row_span(a.slice_ptr, i);
                 const double pi = a.p[i];
-                double acc = pi;
-                for (int k = 0; k < rs.K; ++k) {
-                    const int e = rs.e0 + 32 * k;
-                    acc += a.val[e] * a.p[a.col[e]];
-                }
+                const double acc = spmv_unit_row(a, rs, pi);
                 a.q[i] = acc;
                 v1[0] += pi * acc;
             }
-            if (!(ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf))) break;
-            const double pq = v1[0];
-            if (!(pq > 0.0) || !isfinite(pq)) { status = FV_E_DIVERGED; alpha = 0.0; break; }
-            alpha = rho / pq;
+            if (!(ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                const double pq = tot[0];
+                if (!(pq > 0.0) || !isfinite(pq)) { sc.phase = 3; sc.alpha = 0.0; }
+                else sc.alpha = sc.rho / pq;
+            }
+            __syncthreads();
+            if (sc.phase == 3) break;
             // P3: r^ -= alpha q; r^.r^ and ||D^1/2 r^||^2
+            const double alpha = sc.alpha;
             double v2[2] = {0.0, 0.0};
+#pragma unroll 2
             for (int i = i0; i < re; i += kCgBlock) {
                 const double ri = a.r[i] - alpha * a.q[i];
                 a.r[i] = ri;
@@ -319,26 +377,34 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
                 v2[0] += r2;
                 v2[1] += a.diag[i] * r2;
             }
-            if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf))) break;
-            nr = sqrt(v2[1]);
-            if (!isfinite(nr)) { status = FV_E_DIVERGED; break; }
-            if (nr <= thresh) break;
-            if (it >= a.maxit) { status = FV_E_NOT_CONVERGED; break; }
-            beta = v2[0] / rho;
-            rho = v2[0];
+            if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                sc.nr = sqrt(tot[1]);
+                if (!isfinite(sc.nr)) sc.phase = 3;
+                else if (sc.nr <= sc.thresh) sc.phase = 1;
+                else if (it >= a.maxit) sc.phase = 2;
+                else {
+                    sc.beta = tot[0] / sc.rho;
+                    sc.rho = tot[0];
+                }
+            }
+            __syncthreads();
+            if (sc.phase != 0) break;
         }
         if (ok) {
             // final update of the scaled iterate, then x = D^-1/2 y
-            const double af = (status == FV_E_DIVERGED) ? 0.0 : alpha;
+            const double af = (sc.phase == 3) ? 0.0 : sc.alpha;
             for (int i = i0; i < re; i += kCgBlock) a.x[i] = a.s[i] * (a.y[i] + af * a.p[i]);
         }
     }
-    if (!ok) status = FV_E_TIMEOUT;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int ph = sc.phase;
         a.stats->iters = it;
-        a.stats->status = status;
-        a.stats->res0 = nb > 0.0 ? nr0 / nb : 0.0;
-        a.stats->res = nb > 0.0 ? nr / nb : 0.0;
+        a.stats->status = !ok ? FV_E_TIMEOUT
+                        : ph == 3 ? FV_E_DIVERGED : ph == 2 ? FV_E_NOT_CONVERGED : FV_OK;
+        const bool zero = ph == 4;
+        a.stats->res0 = zero ? 0.0 : sc.nr0 / sc.nb;
+        a.stats->res = zero ? 0.0 : sc.nr / sc.nb;
     }
 }
 
