@@ -236,6 +236,28 @@ fv_status fv_pcg_solve(const fv_mesh *mesh, const double *diag, const double *up
                        const double *b, double *x, const fv_pcg_params *prm,
                        fv_solve_stats *stats);
 
+/* Allocation-free variant of fv_pcg_solve (no counterpart in the paper; it
+ * serves callers of this library).  Same arguments, same kernel and the same
+ * result; the difference is where the solver's work vectors live.
+ * fv_pcg_solve uses memory that fv_mesh_create allocated; this call uses a
+ * fixed array of device memory declared statically in the library (about
+ * 14 MiB, present on every GPU that loads the library until it is
+ * unloaded) and calls no cudaMalloc, cudaFree or other allocating routine.
+ * It is meant for callers that cannot allow device allocation when they
+ * solve: applications whose device memory is all handed out by their own
+ * allocator or pool, and code that runs while a stream capture in global
+ * mode is active in the process, where allocation calls are refused.
+ * Limits: at most 131072 cells and 1048576 row-structure entries of the
+ * mesh; larger meshes return FV_E_INVALID with a message.  The first call
+ * on a device looks up the array's device address (make that first call
+ * before any stream capture).  Every call uses the same array and leaves
+ * its contents behind; the call clears what must start at zero.  Calls that
+ * overlap on the GPU (different streams, other threads) race on the array:
+ * issue them one after another. */
+fv_status fv_pcg_solve_noalloc(const fv_mesh *mesh, const double *diag, const double *upper,
+                               const double *b, double *x, const fv_pcg_params *prm,
+                               fv_solve_stats *stats);
+
 /* Jacobi (right) preconditioned BiCGStab on the non-symmetric LDU matrix
  * (diag, upper, lower) (Sec. 3, momentum systems), same conventions as
  * fv_pcg_solve: lower[f] is the entry in row neighbour[f], column owner[f]. */

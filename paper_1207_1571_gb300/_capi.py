@@ -26,7 +26,7 @@ EXPORTS = [
     "fv_case_get_fields_host", "fv_patch_set_value", "fv_patch_set_face_values", "fv_piso_step",
     "fv_simple_iter", "fv_piso_run_graph", "fv_pcg_solve", "fv_bicgstab_solve", "fv_gauss_grad",
     "fv_ldu_matvec", "fv_last_error", "fv_set_barrier_spin_limit", "fv_case_memory",
-    "fv_profile_enable", "fv_profile_read", "fv_case_last_stats",
+    "fv_profile_enable", "fv_profile_read", "fv_case_last_stats", "fv_pcg_solve_noalloc",
 ]
 PROF_STAGES = ["momentum", "bicgstab", "hbya", "pressure", "pcg", "correct", "other"]
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "fv_simple_iter": [vp, P(fv_simple_params), P(fv_step_stats)],
         "fv_piso_run_graph": [vp, P(fv_piso_params), i32, P(fv_step_stats)],
         "fv_pcg_solve": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
+        "fv_pcg_solve_noalloc": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_bicgstab_solve": [vp, vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_gauss_grad": [vp, vp, vp, vp],
         "fv_ldu_matvec": [vp, vp, vp, vp, vp, vp],

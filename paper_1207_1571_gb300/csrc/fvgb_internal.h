@@ -196,6 +196,14 @@ struct CgProblem {
 fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb);
 
 
+// work vectors of one CG solve supplied by the caller
+struct CgScratch {
+    double *s, *r, *p, *q, *y;   // [N] each
+    double *partials;            // [2][max_blocks][8]
+    int max_blocks;
+    GridBar *bar;
+};
+fv_status launch_pcg_scratch(const fv_mesh *m, const CgProblem &pb, const CgScratch &ws);
 
 struct BicgProblem {
     const double *diag;      // [N]

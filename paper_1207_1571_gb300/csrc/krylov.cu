@@ -669,6 +669,39 @@ fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb)
                        m->stream);
 }
 
+// Same CG launch with caller-supplied work vectors (the allocation-free
+// entry point passes slices of its static scratch array).
+fv_status launch_pcg_scratch(const fv_mesh *m, const CgProblem &pb, const CgScratch &ws)
+{
+    CgArgs a;
+    a.N = m->N;
+    a.slice_ptr = m->slice_ptr;
+    a.col = m->col;
+    a.val = pb.val;
+    a.diag = pb.diag;
+    a.b = pb.b;
+    a.x = pb.x;
+    a.s = ws.s;
+    a.r = ws.r;
+    a.p = ws.p;
+    a.q = ws.q;
+    a.y = ws.y;
+    a.partA = ws.partials;
+    a.partB = ws.partials + (size_t)ws.max_blocks * kParts;
+    a.bar = ws.bar;
+    a.spin = g_spin_limit;
+    a.tol = pb.tol;
+    a.reltol = pb.reltol;
+    a.maxit = pb.maxit;
+    a.stats = pb.stats;
+    const int G = grid_for(m->N, kCgBlock, m->kw.Gcg);
+    FV_CHECK(G <= ws.max_blocks, FV_E_INVALID, "scratch holds partial sums for %d blocks, %d needed",
+             ws.max_blocks, G);
+    FV_CUDA(cudaMemsetAsync(ws.bar, 0, sizeof(GridBar), m->stream));
+    void *args[] = {&a};
+    return coop_launch((const void *)k_pcg, G, kCgBlock, args, m->stream);
+}
+
 fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)
 {
     const KrylovWork &w = m->kw;
