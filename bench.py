@@ -34,11 +34,14 @@ sys.path.insert(0, ROOT)
 METRIC = "PISO steps/s & cell-updates/s; pressure-CG HBM GB/s vs peak; mixed vs FP64"
 UNIT = "cell-updates/s"
 
+BATCH = dict(n_cases=256, seed=7, dt=0.002, n_corr=2)
+
 WORKLOADS = {
     "cavity3d_100": dict(n=100, dim=3, nu=0.01, dt=0.002, n_corr=2, seed=1234),
     "cavity3d_200": dict(n=200, dim=3, nu=0.01, dt=0.001, n_corr=2, seed=1234),
     "cavity3d_40": dict(n=40, dim=3, nu=0.01, dt=0.002, n_corr=2, seed=1234),
     "cavity2d_20": dict(n=20, dim=2, nu=0.1, dt=0.005, n_corr=2, seed=None),
+    "batch256": dict(batch=True),
 }
 # bounded sample of the cavity used for the CPU reference arm
 REF_SAMPLE = "cavity3d_40"
@@ -258,6 +261,45 @@ def run_ours(args, ws, rank, local):
     flops = cg_flops_per_iter(N, F) * iters_p
     fp64_achieved = flops / pcg_s / 1e12 if pcg_s > 0 else None
 
+    # the same steps with the mixed-precision pressure solve
+    mixed = None
+    if not args.no_mixed:
+        cm = P.Case(mesh, w["nu"], P.FV_PREC_MIXED)
+        stm = _capi.fv_step_stats()
+        for _ in range(args.warmup):
+            _capi.check(L.fv_piso_step(cm.h, C.byref(prm), C.byref(stm)), "fv_piso_step", allow=(4,))
+        cm.set_fields(*zero)
+        torch.cuda.synchronize()
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        L.fv_profile_read(None, None, 1)
+        L.fv_profile_enable(1)
+        inner, outer = 0, 0
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                evm[k][0].record(stream)
+            _capi.check(L.fv_piso_step(cm.h, C.byref(prm), None), "fv_piso_step")
+            with torch.cuda.stream(stream):
+                evm[k][1].record(stream)
+            sm_ = cm.last_stats()
+            inner += sum(sm_["iters"][3:])
+            outer += sum(x["outer"] for x in sm_["p"])
+        torch.cuda.synchronize()
+        L.fv_profile_enable(0)
+        pm = (C.c_double * 7)()
+        L.fv_profile_read(pm, None, 1)
+        tm = allmax(ws, sum(a.elapsed_time(b) for a, b in evm) / 1e3, "cuda")
+        # difference of the fields after the timed steps (both from rest)
+        ua, pa, fa = case.get_fields()
+        ub, pb_, fb = cm.get_fields()
+        d_ = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        mixed = {"value": ws * N * args.steps / tm, "unit": UNIT, "steps_per_s": args.steps / tm,
+                 "speedup_vs_fp64": t / tm, "inner_iterations": inner, "outer_passes": outer,
+                 "cg_ms": pm[4], "us_per_inner_iter": 1e3 * pm[4] / inner if inner else None,
+                 "rel_l2_vs_fp64_gpu": {"u": d_(ub, ua), "p": d_(pb_, pa), "phi": d_(fb, fa)}}
+        cm.close()
+
     # end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -307,11 +349,23 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(sum(prof_n[k] for k in range(7))),
         "clocks": clk_sum,
         "e2e": e2e,
+        "mixed": mixed,
         "memory_bytes": case.memory_bytes(),
         "statuses": sorted(set(statuses)),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload)
+        cb, ofields = cpu_baseline(args.workload)
+        out["cpu_baseline"] = cb
+        # error of the first step from rest against the oracle's (FP64 and mixed)
+        errs = {}
+        for name, prec in (("fp64", P.FV_PREC_FP64), ("mixed", P.FV_PREC_MIXED)):
+            c1 = P.Case(mesh, w["nu"], prec)
+            c1.piso_step(w["dt"], w["n_corr"], p_ref_cell=ref)
+            g = c1.get_fields_host()
+            errs[name] = {k: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+                          for k, a, b in zip(("u", "p", "phi"), g, ofields)}
+            c1.close()
+        out["first_step_rel_l2_vs_oracle"] = errs
     return out
 
 
@@ -326,9 +380,104 @@ def cpu_baseline(workload):
     t0 = time.perf_counter()
     oc.piso_step(w["dt"], w["n_corr"], p_ref_cell=m.corner_cell)
     t = time.perf_counter() - t0
-    return {"value": m.n_cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 PISO step from rest of {workload} ({m.n_cells} cells), "
-                      f"single-threaded FP64 C oracle, {t:.1f} s"}
+    cb = {"value": m.n_cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"1 PISO step from rest of {workload} ({m.n_cells} cells), "
+                    f"single-threaded FP64 C oracle, {t:.1f} s"}
+    return cb, oc.get_fields()
+
+
+# ----------------------------------------------------------------- batch --
+
+def run_batch(args, ws, rank):
+    """256 independent 2-D cavities (n ~ U[32,128], Re log-uniform in
+    [10,1000], seed 7): batched steps (one launch per PISO stage, CUDA graph,
+    autotuned schedule) against a per-case loop of the single-case solver."""
+    import torch
+    import ctypes as C
+    import meshgen as mg
+    from paper_1207_1571_gb300 import build as B
+    import paper_1207_1571_gb300 as P
+    from paper_1207_1571_gb300 import _capi
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    L = P.load()
+    spec = mg.batch_cases(BATCH["n_cases"], BATCH["seed"])
+    ms = [mg.cavity2d(n) for n, _ in spec]
+    nus = [nu for _, nu in spec]
+    refs = [m.corner_cell for m in ms]
+    ncell = sum(m.n_cells for m in ms)
+    dt, nc = BATCH["dt"], BATCH["n_corr"]
+    prec = P.FV_PREC_MIXED if args.precision == "mixed" else P.FV_PREC_FP64
+    warm = P.Batch(ms, nus, refs, prec)
+    key = f"{torch.cuda.get_device_name()}|batch{len(ms)}|seed{BATCH['seed']}|{args.precision}"
+    tuned = warm.autotune(dt, nc, cache_path=os.path.join(ROOT, "paper_1207_1571_gb300", "_build",
+                                                           "autotune.json"), key=key)
+    for _ in range(args.warmup):
+        warm.run_graph(1, dt, nc, stats=False)
+    torch.cuda.synchronize()
+    warm.close()
+    bt = P.Batch(ms, nus, refs, prec, stream=torch.cuda.Stream())
+    bt.set_schedule(tuned["schedule"])
+    prm = P.Case.piso_params(dt, nc)
+    stream = bt.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # capture once outside the timed region
+    _capi.check(L.fv_batch_run_graph(bt.h, C.byref(prm), 0, None), "fv_batch_run_graph")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[k][0].record(stream)
+            _capi.check(L.fv_batch_run_graph(bt.h, C.byref(prm), 1, None), "fv_batch_run_graph")
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    t = allmax(ws, sum(a.elapsed_time(b) for a, b in ev) / 1e3, "cuda")
+    st = bt.piso_step(dt, nc)          # one more step for the statistics
+    its = [sum(s["iters"][3:]) for s in st]
+    # per-case loop of the single-case solver, same cases from rest
+    loop_steps = max(1, min(2, args.steps))
+    meshes = [P.Mesh(m, renumber=True, stream=stream) for m in ms]
+    cases = [P.Case(mm, nu) for mm, nu in zip(meshes, nus)]
+    prms = [P.Case.piso_params(dt, nc, p_ref_cell=r) for r in refs]
+    for c, pr in zip(cases, prms):
+        L.fv_piso_step(c.h, C.byref(pr), None)
+    torch.cuda.synchronize()
+    for c in cases:
+        c.set_fields(torch.zeros(3, c.mesh.N, dtype=torch.float64, device="cuda"),
+                     torch.zeros(c.mesh.N, dtype=torch.float64, device="cuda"),
+                     torch.zeros(c.mesh.M, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(loop_steps):
+        for c, pr in zip(cases, prms):
+            _capi.check(L.fv_piso_step(c.h, C.byref(pr), None), "fv_piso_step")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_loop = e0.elapsed_time(e1) / 1e3
+    v_loop = ncell * loop_steps / t_loop
+    value = ws * ncell * args.steps / t
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == P.FV_PREC_FP64 else "f64+f32", "data": "synthetic",
+            "steps_per_s": args.steps / t,
+            "config": {"workload": "batch256: 256 independent 2-D lid-driven cavities, n_i in "
+                                   "[32,128], Re_i log-uniform in [10,1000] (seed 7), dt 0.002, "
+                                   "PISO 2 correctors", "cells": ncell, "cases": len(ms),
+                       "schedule": tuned, "l2": "flushed between timed steps; steps from rest",
+                       "precision": args.precision},
+            "per_case_loop": {"value": v_loop, "unit": UNIT, "steps": loop_steps,
+                              "ms_per_step": 1e3 * t_loop / loop_steps},
+            "speedup_vs_per_case_loop": value / ws / v_loop,
+            "cg_iterations_next_step": {"total": int(sum(its)), "max_case": int(max(its))},
+            "clocks": clk.summary(), "gpu_launches": 10 * args.steps, "roofline": None}
 
 
 # ------------------------------------------------------------- reference --
@@ -370,10 +519,15 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cavity3d_100")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="batch workload only")
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
+    elif WORKLOADS[args.workload].get("batch"):
+        out = run_batch(args, ws, rank)
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:

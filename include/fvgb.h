@@ -89,10 +89,13 @@ typedef struct fv_case fv_case;
 
 /* Per linear solve. */
 typedef struct {
-    int32_t iters;     /* Krylov iterations (SMVPs for CG) */
+    int32_t iters;     /* Krylov iterations (SMVPs for CG; FP32 inner ones for mixed) */
     int32_t status;    /* fv_status of this solve */
     double res0;       /* initial ||b - A x0||_2 / ||b||_2 */
-    double res;        /* final   ||r||_2 / ||b||_2 (recursively updated r) */
+    double res;        /* final ||r||_2 / ||b||_2: recursively updated r (FP64 CG,
+                          BiCGStab) or the true FP64 residual (mixed precision) */
+    int32_t outer;     /* FP64 residual passes (mixed precision), else 1 */
+    int32_t pad_;
 } fv_solve_stats;
 
 #define FV_MAX_CORR 8
@@ -221,6 +224,43 @@ fv_status fv_case_last_stats(fv_case *cs, fv_step_stats *stats);
 fv_status fv_piso_run_graph(fv_case *cs, const fv_piso_params *prm, int32_t n_steps,
                             fv_step_stats *stats);
 
+/* ------------------------------------------------------------ batches -- */
+
+/* Many independent cases advanced together (not in the paper, which runs one
+ * case per GPU).  The n meshes (host descriptions, copied; every mesh must be
+ * connected) are joined into one block-diagonal mesh renumbered by reverse
+ * Cuthill-McKee; case c has kinematic viscosity nu[c] and, when
+ * p_ref_cells[c] >= 0 (caller's numbering of that case), that reference
+ * pressure cell (p_ref_cells may be NULL for cases with outlets).  Every PISO
+ * stage is one launch over all cases: assembly and corrections over all
+ * cells, the Krylov solves one block per case from a queue of cases ordered
+ * by size.  precision: FV_PREC_FP64 or FV_PREC_MIXED (pressure solve as in
+ * fv_pcg_solve_mixed, per case).  stream as in fv_mesh_create. */
+typedef struct fv_batch fv_batch;
+fv_status fv_batch_create(const fv_mesh_desc *descs, int32_t n, const double *nu,
+                          const int32_t *p_ref_cells, int32_t precision, void *stream,
+                          fv_batch **out);
+fv_status fv_batch_destroy(fv_batch *bt);
+/* One PISO step of every case; prm->p_ref_cell is ignored (per-case pins
+ * come from fv_batch_create).  per_case: host [n] or NULL (no sync). */
+fv_status fv_batch_piso_step(fv_batch *bt, const fv_piso_params *prm, fv_step_stats *per_case);
+/* Capture one batched step into a CUDA graph (once per parameter set and
+ * schedule) and replay it n_steps times. */
+fv_status fv_batch_run_graph(fv_batch *bt, const fv_piso_params *prm, int32_t n_steps,
+                             fv_step_stats *per_case);
+/* Fields of case c in its own original numbering: u [3][N_c], p [N_c],
+ * phi [F_c + B_c] (host, any may be NULL).  Synchronous. */
+fv_status fv_batch_get_fields(const fv_batch *bt, int32_t c, double *u, double *p, double *phi);
+/* Schedules of the per-case Krylov kernels: info = {threads per block, rows
+ * per thread per loop trip, block reduction (0 shuffle tree, 1 shared-memory
+ * staging), number of schedules}. */
+fv_status fv_batch_schedule_info(int32_t schedule, int32_t *info /* host [4] */);
+fv_status fv_batch_set_schedule(fv_batch *bt, int32_t schedule);
+/* Autotuner: time one PISO step with every schedule from the current state
+ * (restored after each trial), keep the fastest; best (host, may be NULL)
+ * receives its index, ms (host [number of schedules] or NULL) the times. */
+fv_status fv_batch_autotune(fv_batch *bt, const fv_piso_params *prm, int32_t *best, double *ms);
+
 /* ------------------------------------------------------------ solvers -- */
 
 /* Jacobi-preconditioned CG on the symmetric matrix (diag, upper) in LDU form
@@ -257,6 +297,18 @@ fv_status fv_pcg_solve(const fv_mesh *mesh, const double *diag, const double *up
 fv_status fv_pcg_solve_noalloc(const fv_mesh *mesh, const double *diag, const double *upper,
                                const double *b, double *x, const fv_pcg_params *prm,
                                fv_solve_stats *stats);
+
+/* The same solve with the mixed-precision method of FV_PREC_MIXED cases (not
+ * in the paper): defect correction in FP64 -- true residual b - A x with the
+ * FP64 matrix, its norm and the stopping test, x += correction -- around an
+ * FP32 Jacobi-CG on an FP32 copy of the symmetrically scaled matrix (inner
+ * dot products summed in FP64 across threads).  Stops on the true FP64
+ * residual: ||b - A x||_2 <= max(tol ||b||_2, reltol ||r0||_2); maxit bounds
+ * the FP32 inner iterations.  Arguments as fv_pcg_solve; diag and upper are
+ * not modified. */
+fv_status fv_pcg_solve_mixed(const fv_mesh *mesh, const double *diag, const double *upper,
+                             const double *b, double *x, const fv_pcg_params *prm,
+                             fv_solve_stats *stats);
 
 /* Jacobi (right) preconditioned BiCGStab on the non-symmetric LDU matrix
  * (diag, upper, lower) (Sec. 3, momentum systems), same conventions as

@@ -22,7 +22,8 @@ from . import _capi
 from ._capi import (FV_PREC_FP64, FV_PREC_MIXED, FV_E_NOT_CONVERGED, FV_OK, FvError,  # noqa
                     check, load)
 
-__all__ = ["Mesh", "Case", "mesh_plan", "load", "FvError", "FV_PREC_FP64", "FV_PREC_MIXED"]
+__all__ = ["Mesh", "Case", "Batch", "mesh_plan", "load", "FvError", "FV_PREC_FP64",
+           "FV_PREC_MIXED"]
 
 
 def _desc(m, renumber: bool):
@@ -69,7 +70,7 @@ def _ptr(t) -> Optional[int]:
 
 
 def _solve_dict(s) -> dict:
-    return dict(iters=s.iters, status=s.status, res0=s.res0, res=s.res)
+    return dict(iters=s.iters, status=s.status, res0=s.res0, res=s.res, outer=s.outer)
 
 
 def _step_dict(s: _capi.fv_step_stats) -> dict:
@@ -158,6 +159,17 @@ class Mesh:
         check(rc, "fv_pcg_solve", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
         return _solve_dict(st)
 
+    def pcg_solve_mixed(self, diag, upper, b, x, tol=1e-6, reltol=0.0, maxit=10000) -> dict:
+        """FP32-inside-FP64 defect-correction CG (fv_pcg_solve_mixed)."""
+        prm = _capi.fv_pcg_params(tol, reltol, maxit, 0)
+        st = _capi.fv_solve_stats()
+        self._enter(diag, upper, b, x)
+        rc = self.L.fv_pcg_solve_mixed(self.h, diag.data_ptr(), _ptr(upper), b.data_ptr(),
+                                       x.data_ptr(), C.byref(prm), C.byref(st))
+        self._leave()
+        check(rc, "fv_pcg_solve_mixed", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
+        return _solve_dict(st)
+
     def bicgstab_solve(self, diag, upper, lower, b, x, tol=1e-10, reltol=0.0, maxit=1000) -> dict:
         prm = _capi.fv_pcg_params(tol, reltol, maxit, 0)
         st = _capi.fv_solve_stats()
@@ -240,6 +252,17 @@ class Case:
                                              1 if original_order else 0), "fv_case_get_fields_host")
         return u, p, phi
 
+    def save(self, path: str, **extra):
+        """Checkpoint: fields in the caller's numbering, as a .npz file."""
+        u, p, phi = self.get_fields_host()
+        np.savez(path, u=u, p=p, phi=phi, nu=self.nu, **extra)
+
+    def load(self, path: str) -> dict:
+        """Restore fields saved by :meth:`save`; returns the extra entries."""
+        d = np.load(path)
+        self.set_fields_host(d["u"], d["p"], d["phi"])
+        return {k: d[k] for k in d.files if k not in ("u", "p", "phi", "nu")}
+
     def set_patch(self, q: int, u=(0.0, 0.0, 0.0), p: float = 0.0):
         uu = np.ascontiguousarray(u, dtype=np.float64)
         check(self.L.fv_patch_set_value(self.h, q, uu.ctypes.data, float(p)), "fv_patch_set_value")
@@ -296,3 +319,116 @@ class Case:
         rc = self.L.fv_simple_iter(self.h, C.byref(prm), C.byref(s))
         check(rc, "fv_simple_iter", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
         return _step_dict(s)
+
+
+class Batch:
+    """Many independent cases advanced together (``fv_batch_create``)."""
+
+    def __init__(self, meshes, nu, p_ref_cells=None, precision: int = FV_PREC_FP64, stream=None):
+        import torch
+        self.L = load()
+        self.n = len(meshes)
+        self.meshes = meshes
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        descs = (_capi.fv_mesh_desc * self.n)()
+        self._keep = []
+        for k, m in enumerate(meshes):
+            d, keep = _desc(m, True)
+            descs[k] = d
+            self._keep.append(keep)
+        nu_a = np.ascontiguousarray(nu, dtype=np.float64)
+        ref = None if p_ref_cells is None else np.ascontiguousarray(p_ref_cells, dtype=np.int32)
+        h = C.c_void_p()
+        check(self.L.fv_batch_create(descs, self.n, nu_a.ctypes.data,
+                                     None if ref is None else ref.ctypes.data, precision,
+                                     C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+              "fv_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fv_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stats(self, arr):
+        return [_step_dict(arr[k]) for k in range(self.n)]
+
+    def piso_step(self, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10, u_maxit=1000,
+                  stats=True):
+        prm = Case.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, -1, 0.0)
+        arr = (_capi.fv_step_stats * self.n)() if stats else None
+        self._torch_wait()
+        rc = self.L.fv_batch_piso_step(self.h, C.byref(prm), arr)
+        check(rc, "fv_batch_piso_step", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
+        return self._stats(arr) if stats else None
+
+    def run_graph(self, n_steps, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10,
+                  u_maxit=1000, stats=True):
+        prm = Case.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, -1, 0.0)
+        arr = (_capi.fv_step_stats * self.n)() if stats else None
+        self._torch_wait()
+        rc = self.L.fv_batch_run_graph(self.h, C.byref(prm), n_steps, arr)
+        check(rc, "fv_batch_run_graph", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
+        return self._stats(arr) if stats else None
+
+    def _torch_wait(self):
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+
+    def get_fields(self, c):
+        m = self.meshes[c]
+        u, p, phi = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_faces)
+        check(self.L.fv_batch_get_fields(self.h, c, u.ctypes.data, p.ctypes.data, phi.ctypes.data),
+              "fv_batch_get_fields")
+        return u, p, phi
+
+    @staticmethod
+    def schedules():
+        L = load()
+        a = np.zeros(4, np.int32)
+        check(L.fv_batch_schedule_info(0, a.ctypes.data), "fv_batch_schedule_info")
+        out = []
+        for k in range(int(a[3])):
+            check(L.fv_batch_schedule_info(k, a.ctypes.data), "fv_batch_schedule_info")
+            out.append(dict(block=int(a[0]), rows_per_trip=int(a[1]), reduction=int(a[2])))
+        return out
+
+    def set_schedule(self, k: int):
+        check(self.L.fv_batch_set_schedule(self.h, k), "fv_batch_set_schedule")
+
+    def autotune(self, dt, n_corr=2, p_tol=1e-6, cache_path=None, key=None) -> dict:
+        """Pick the fastest schedule (fv_batch_autotune); with cache_path, the
+        choice is stored in / reused from a JSON file under key."""
+        import json
+        import os
+        if cache_path and key and os.path.exists(cache_path):
+            try:
+                cache = json.load(open(cache_path))
+                if key in cache:
+                    self.set_schedule(int(cache[key]["schedule"]))
+                    return dict(cache[key], cached=True)
+            except Exception:
+                pass
+        prm = Case.piso_params(dt, n_corr, p_tol)
+        ns = len(self.schedules())
+        best = C.c_int32()
+        ms = (C.c_double * ns)()
+        self._torch_wait()
+        check(self.L.fv_batch_autotune(self.h, C.byref(prm), C.byref(best), ms), "fv_batch_autotune")
+        res = dict(schedule=best.value, ms=[ms[k] for k in range(ns)],
+                   **self.schedules()[best.value])
+        if cache_path and key:
+            try:
+                cache = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
+            except Exception:
+                cache = {}
+            cache[key] = res
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            json.dump(cache, open(cache_path, "w"), indent=1)
+        return dict(res, cached=False)

@@ -27,6 +27,9 @@ EXPORTS = [
     "fv_simple_iter", "fv_piso_run_graph", "fv_pcg_solve", "fv_bicgstab_solve", "fv_gauss_grad",
     "fv_ldu_matvec", "fv_last_error", "fv_set_barrier_spin_limit", "fv_case_memory",
     "fv_profile_enable", "fv_profile_read", "fv_case_last_stats", "fv_pcg_solve_noalloc",
+    "fv_pcg_solve_mixed", "fv_batch_create", "fv_batch_destroy", "fv_batch_piso_step",
+    "fv_batch_run_graph", "fv_batch_get_fields", "fv_batch_schedule_info", "fv_batch_set_schedule",
+    "fv_batch_autotune",
 ]
 PROF_STAGES = ["momentum", "bicgstab", "hbya", "pressure", "pcg", "correct", "other"]
 
@@ -46,7 +49,7 @@ class fv_mesh_desc(C.Structure):
 
 class fv_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("res0", C.c_double),
-                ("res", C.c_double)]
+                ("res", C.c_double), ("outer", C.c_int32), ("pad_", C.c_int32)]
 
 
 class fv_step_stats(C.Structure):
@@ -108,6 +111,15 @@ def load(path: str = LIB_PATH):
         "fv_piso_run_graph": [vp, P(fv_piso_params), i32, P(fv_step_stats)],
         "fv_pcg_solve": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_pcg_solve_noalloc": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
+        "fv_pcg_solve_mixed": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
+        "fv_batch_create": [vp, i32, vp, vp, i32, vp, P(vp)],
+        "fv_batch_destroy": [vp],
+        "fv_batch_piso_step": [vp, P(fv_piso_params), vp],
+        "fv_batch_run_graph": [vp, P(fv_piso_params), i32, vp],
+        "fv_batch_get_fields": [vp, i32, vp, vp, vp],
+        "fv_batch_schedule_info": [i32, vp],
+        "fv_batch_set_schedule": [vp, i32],
+        "fv_batch_autotune": [vp, P(fv_piso_params), vp, vp],
         "fv_bicgstab_solve": [vp, vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_gauss_grad": [vp, vp, vp, vp],
         "fv_ldu_matvec": [vp, vp, vp, vp, vp, vp],

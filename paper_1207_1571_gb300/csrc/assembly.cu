@@ -59,6 +59,7 @@ static int blocks_for(int n) { return (n + kAsmBlock - 1) / kAsmBlock; }
 struct MomArgs {
     const double *u, *p, *phi, *ub, *pb, *gradU;
     double nu, dt_inv, alpha_u;
+    const double *nu_cell;   // per-cell viscosity (batched cases) or nullptr
     double *Md, *Mo, *src, *gradp;
 };
 
@@ -70,6 +71,9 @@ __global__ void __launch_bounds__(kAsmBlock) k_momentum(MeshView m, MomArgs a)
     const int s = i >> 5;
     const int e0 = m.slice_ptr[s] + (i & 31), K = (m.slice_ptr[s + 1] - m.slice_ptr[s]) >> 5;
     const double vdt = m.V[i] * a.dt_inv;
+    // both cells of a face belong to the same case, so the owner's value is
+    // the face's
+    const double nu = a.nu_cell ? a.nu_cell[i] : a.nu;
     double diag = vdt;
     double src0 = vdt * a.u[i], src1 = vdt * a.u[N + i], src2 = vdt * a.u[2 * N + i];
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(kAsmBlock) k_momentum(MeshView m, MomArgs a)
         const double wO = own ? 1.0 - w : w;       // weight of the other cell
         const double sg = own ? 1.0 : -1.0;
         const double Fo = sg * a.phi[f];           // flux out of this cell
-        const double D = a.nu * m.magSf[f] * m.delta[f];
+        const double D = nu * m.magSf[f] * m.delta[f];
         diag += Fo * wS;
         diag += D;
         a.Mo[e] = Fo * wO - D;
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(kAsmBlock) k_momentum(MeshView m, MomArgs a)
                 const double gx = w * G[lo] + (1.0 - w) * G[hi];
                 const double gy = w * G[N + lo] + (1.0 - w) * G[N + hi];
                 const double gz = w * G[2 * N + lo] + (1.0 - w) * G[2 * N + hi];
-                t[cc] = a.nu * m.magSf[f] * (k0 * gx + k1 * gy + k2 * gz);
+                t[cc] = nu * m.magSf[f] * (k0 * gx + k1 * gy + k2 * gz);
             }
             src0 += sg * t[0];
             src1 += sg * t[1];
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(kAsmBlock) k_momentum(MeshView m, MomArgs a)
             diag += a.phi[fb];
             pbv = a.pb[b];
         } else {
-            const double D = a.nu * m.magSf[fb] * m.delta[fb];
+            const double D = nu * m.magSf[fb] * m.delta[fb];
             const double Fb = a.phi[fb];
             diag += D;
             const double u0 = a.ub[b], u1 = a.ub[m.B + b], u2 = a.ub[2 * m.B + b];
@@ -226,6 +230,7 @@ struct PresArgs {
     const double *HbyA, *rAU, *ub, *pb, *gradp;
     int ref;
     double p_ref;
+    const int8_t *pin;       // per-cell reference flags (batched cases) or nullptr
     double *Pd, *Po, *b, *phis, *af, *nof;
 };
 
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kAsmBlock) k_pressure(MeshView m, PresArgs a)
         a.phis[fb] = ph;
         bb -= ph;
     }
-    if (i == a.ref) {
+    if (i == a.ref || (a.pin && a.pin[i])) {
         bb += diag * a.p_ref;
         diag *= 2.0;
     }
@@ -654,7 +659,7 @@ fv_status launch_momentum(const fv_case *c, const StepArgs &s)
 {
     const fv_mesh *m = c->mesh;
     MomArgs a{c->u, c->p, c->phi, c->ub, c->pb, c->gradU, c->nu, s.dt_inv, s.alpha_u,
-              c->Md, c->Mo, c->src, c->gradp};
+              c->nu_cell, c->Md, c->Mo, c->src, c->gradp};
     k_momentum<<<blocks_for(m->N), kAsmBlock, 0, m->stream>>>(view(m), a);
     LAUNCH_CHECK();
     return FV_OK;
@@ -672,7 +677,7 @@ fv_status launch_hbya(const fv_case *c)
 fv_status launch_pressure(const fv_case *c, const StepArgs &s)
 {
     const fv_mesh *m = c->mesh;
-    PresArgs a{c->HbyA, c->rAU, c->ub, c->pb, c->gradp, s.ref_cell, s.p_ref,
+    PresArgs a{c->HbyA, c->rAU, c->ub, c->pb, c->gradp, s.ref_cell, s.p_ref, c->pin,
                c->Pd, c->Po, c->pbv, c->phis, c->af, c->nof};
     k_pressure<<<blocks_for(m->N), kAsmBlock, 0, m->stream>>>(view(m), a);
     LAUNCH_CHECK();

@@ -56,6 +56,20 @@ void fill_solve(fv_solve_stats *o, const DevSolveStats &d)
     o->status = d.status;
     o->res0 = d.res0;
     o->res = d.res;
+    o->outer = d.outer;
+    o->pad_ = 0;
+}
+
+// pressure solve of a step: FP64 CG, or the mixed-precision method
+fv_status launch_pressure_solve(const fv_case *c, double tol, double reltol, int maxit,
+                                DevSolveStats *st)
+{
+    if (c->precision == FV_PREC_MIXED) {
+        MixedProblem mp{c->Pd, c->Po, c->pbv, c->p, tol, reltol, maxit, st};
+        return launch_pcg_mixed(c->mesh, mp);
+    }
+    CgProblem cp{c->Pd, c->Po, c->pbv, c->p, tol, reltol, maxit, st};
+    return launch_pcg(c->mesh, cp);
 }
 
 int worse(int a, int b)
@@ -115,9 +129,8 @@ fv_status piso_enqueue(fv_case *c, const fv_piso_params *prm, int ref)
     for (int k = 0; k < prm->n_corr; ++k) {
         STAGE(FV_PROF_HBYA, 1, launch_hbya(c));
         STAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
-        CgProblem cp{c->Pd, c->Po, c->pbv, c->p, prm->p_tol, 0.0, prm->p_maxit,
-                     c->dstats + 3 + k};
-        STAGE(FV_PROF_PCG, 1, launch_pcg(m, cp));
+        STAGE(FV_PROF_PCG, 1,
+              launch_pressure_solve(c, prm->p_tol, 0.0, prm->p_maxit, c->dstats + 3 + k));
         STAGE(FV_PROF_CORRECT, 1, launch_correct_piso(c));
     }
     return FV_OK;
@@ -388,8 +401,8 @@ extern "C" fv_status fv_simple_iter(fv_case *c, const fv_simple_params *prm, fv_
     STAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
     STAGE(FV_PROF_OTHER, 2, launch_simple_residuals_p(c));
     FV_CUDA(cudaMemcpyAsync(c->pold, c->p, sizeof(double) * m->N, cudaMemcpyDeviceToDevice, m->stream));
-    CgProblem cp{c->Pd, c->Po, c->pbv, c->p, prm->p_tol, prm->p_reltol, prm->p_maxit, c->dstats + 3};
-    STAGE(FV_PROF_PCG, 1, launch_pcg(m, cp));
+    STAGE(FV_PROF_PCG, 1,
+          launch_pressure_solve(c, prm->p_tol, prm->p_reltol, prm->p_maxit, c->dstats + 3));
     STAGE(FV_PROF_CORRECT, 2, launch_correct_simple(c, prm->alpha_p));
     c->last_np = 1;
     c->last_simple = true;
@@ -445,6 +458,25 @@ extern "C" fv_status fv_pcg_solve(const fv_mesh *mc, const double *diag, const d
     if (st != FV_OK) return st;
     CgProblem cp{diag, m->kw.val, b, x, prm->tol, prm->reltol, prm->maxit, m->kw.stats};
     if ((st = launch_pcg(m, cp)) != FV_OK) return st;
+    DevSolveStats h;
+    FV_CUDA(cudaMemcpyAsync(&h, m->kw.stats, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
+    FV_CUDA(cudaStreamSynchronize(m->stream));
+    if (stats) fill_solve(stats, h);
+    return (fv_status)h.status;
+}
+
+extern "C" fv_status fv_pcg_solve_mixed(const fv_mesh *mc, const double *diag, const double *upper,
+                                        const double *b, double *x, const fv_pcg_params *prm,
+                                        fv_solve_stats *stats)
+{
+    FV_CHECK(mc && diag && b && x && prm, FV_E_INVALID, "NULL argument");
+    FV_CHECK(mc->F == 0 || upper, FV_E_INVALID, "upper is NULL");
+    FV_CHECK(prm->maxit >= 0 && prm->tol >= 0.0 && prm->reltol >= 0.0, FV_E_INVALID, "bad params");
+    fv_mesh *m = const_cast<fv_mesh *>(mc);
+    fv_status st = launch_ldu_to_sell(m, upper, upper, m->kw.val);
+    if (st != FV_OK) return st;
+    MixedProblem mp{diag, m->kw.val, b, x, prm->tol, prm->reltol, prm->maxit, m->kw.stats};
+    if ((st = launch_pcg_mixed(m, mp)) != FV_OK) return st;
     DevSolveStats h;
     FV_CUDA(cudaMemcpyAsync(&h, m->kw.stats, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
     FV_CUDA(cudaStreamSynchronize(m->stream));

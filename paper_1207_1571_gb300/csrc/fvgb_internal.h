@@ -74,6 +74,8 @@ struct DevSolveStats {
     int32_t status;
     double res0;
     double res;
+    int32_t outer;
+    int32_t pad;
 };
 
 // Grid barrier state (bounded spin, see krylov.cu).
@@ -94,6 +96,8 @@ struct KrylovWork {
     double *dinv = nullptr;  // [N] (BiCGStab) / scaling s (CG)
     double *r = nullptr, *p = nullptr, *q = nullptr, *y = nullptr;   // CG [N]
     double *bv[9] = {};      // BiCGStab: r, rh, p, v, y(s), z, t ... per component [3N] each
+    float *val32 = nullptr;      // FP32 scaled SELL values (mixed precision, lazily)
+    float *f32[6] = {};          // FP32 inner vectors r, p, q, e, w, v [N]
     double *partials = nullptr;  // [2][G][8]
     GridBar *bar = nullptr;
     DevSolveStats *stats = nullptr;  // [4] scratch for stand-alone calls
@@ -140,6 +144,8 @@ struct fv_case {
     float *Po32 = nullptr;
     double *resid = nullptr;
     double *tmp = nullptr;                   // field exchange temporary [max(3N, M)]
+    double *nu_cell = nullptr;               // per-cell viscosity (batched cases) or nullptr
+    int8_t *pin = nullptr;                   // per-cell reference-pressure flags or nullptr
     // per-step statistics
     fvgb::DevSolveStats *dstats = nullptr;   // [3 + FV_MAX_CORR + 2]
     double *dsimple = nullptr;               // SIMPLE residual partials/finals
@@ -195,6 +201,17 @@ struct CgProblem {
 };
 fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb);
 
+// FP32-inside-FP64 defect-correction CG (the FP64 values are not modified)
+struct MixedProblem {
+    const double *diag;
+    const double *val;       // SELL off-diagonals, unscaled FP64
+    const double *b;
+    double *x;
+    double tol, reltol;
+    int maxit;               // budget of inner iterations
+    DevSolveStats *stats;
+};
+fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb);
 
 // work vectors of one CG solve supplied by the caller
 struct CgScratch {

@@ -405,6 +405,284 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
         const bool zero = ph == 4;
         a.stats->res0 = zero ? 0.0 : sc.nr0 / sc.nb;
         a.stats->res = zero ? 0.0 : sc.nr / sc.nb;
+        a.stats->outer = 1;
+    }
+}
+
+// ------------------------------------------------------ mixed precision --
+//
+// FP32 Jacobi-CG with reliable updates and one deflation vector, inside FP64
+// defect correction (not in the paper, whose Fermi code is FP64 throughout).
+//
+// * FP64: the true residual r = b - A x with the FP64 matrix, its norm, the
+//   stopping test ||b - A x|| <= max(tol ||b||, reltol ||r0||), the solution
+//   x, and all reductions across threads and blocks.
+// * FP32: the CG recurrences (p, q, r^ and the correction e) on an FP32 copy
+//   of the symmetrically scaled matrix A^ = D^-1/2 A D^-1/2; products are
+//   summed in FP32 over a thread's rows.
+// * Reliable updates: when the FP32 residual has fallen by kReliable since the
+//   last refresh, or predicts convergence, or p.A^p is not positive, e is
+//   folded into x and the residual is recomputed in FP64; the search
+//   direction is kept (restarted only after a non-positive curvature).
+// * Deflation: a pressure matrix pinned at one reference cell (closed
+//   domains) has one eigenvalue of order 1/N (the constant mode), which FP32
+//   CG cannot resolve.  Search directions are kept A^-orthogonal to
+//   w = D^1/2 1 (p = r^ + beta p - w (v.r^)/mu with v = A^ w = D^-1/2 A 1,
+//   mu = 1.A.1) and every refresh first removes the residual's component
+//   along the mode with the constant shift x += (1.r)/mu.
+
+constexpr double kReliable = 0.1;
+
+struct MixArgs {
+    int N;
+    const int32_t *slice_ptr, *col;
+    const double *val;      // FP64 off-diagonals (unscaled), read only
+    float *val32;           // FP32 scaled off-diagonals (written in setup)
+    const double *diag, *b;
+    double *x, *s, *r64, *a1;
+    float *r, *p, *q, *e, *w, *v;
+    double *partA, *partB;
+    GridBar *bar;
+    long long spin;
+    double tol, reltol;
+    int maxit;
+    DevSolveStats *stats;
+};
+
+struct MixScalars {
+    double nb, nr0, nr, thresh, rho, rho_ref, ratio, alpha, beta, mu, delta, shift;
+    int phase;       // 0 run, 1 converged, 2 iteration budget used, 3 breakdown, 4 zero rhs
+    int refresh;     // 1: refresh after this iteration, 2: refresh and restart p
+    int restart;     // restart the search direction at the next iteration
+    int bad;         // consecutive forced refreshes without progress
+    int deflate;
+};
+
+__device__ __forceinline__ float spmv32_unit_row(const MixArgs &a, const RowSpan &rs, float pi)
+{
+    float acc = pi;
+    if (rs.K <= 6) {
+        int c[6];
+        float v[6], x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) { c[k] = a.col[rs.e0 + 32 * k]; v[k] = a.val32[rs.e0 + 32 * k]; }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) x[k] = a.p[c[k]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) acc = fmaf(v[k], x[k], acc);
+    } else {
+        for (int k = 0; k < rs.K; ++k) {
+            const int e = rs.e0 + 32 * k;
+            acc = fmaf(a.val32[e], a.p[a.col[e]], acc);
+        }
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
+{
+    __shared__ double buf[3][kCgBlock];
+    __shared__ double tot[3];
+    __shared__ MixScalars sc;
+    const int N = a.N;
+    const int nsl = (N + 31) >> 5;
+    const int chunk = ((nsl + gridDim.x - 1) / gridDim.x) * 32;
+    const int rb = blockIdx.x * chunk;
+    const int re = min(N, rb + chunk);
+    const int i0 = rb + threadIdx.x;
+    unsigned gen = 0;
+    bool ok = true;
+    int it = 0, outer = 0;
+
+    // S1: scaling
+    for (int i = i0; i < re; i += kCgBlock) a.s[i] = 1.0 / sqrt(a.diag[i]);
+    ok = grid_sync(a.bar, gen, a.spin);
+    // S2: FP32 scaled matrix, A 1 (FP64), w = D^1/2 1, v = D^-1/2 A 1, mu = 1.A.1
+    if (ok) {
+        double v1[1] = {0.0};
+        for (int i = i0; i < re; i += kCgBlock) {
+            const RowSpan rs = row_span(a.slice_ptr, i);
+            const double si = a.s[i];
+            double row = a.diag[i];
+            for (int k = 0; k < rs.K; ++k) {
+                const int e = rs.e0 + 32 * k;
+                const double v = a.val[e];
+                row += v;
+                a.val32[e] = (float)(v * si * a.s[a.col[e]]);
+            }
+            a.a1[i] = row;
+            a.w[i] = (float)(1.0 / si);
+            a.v[i] = (float)(si * row);
+            v1[0] += row;
+        }
+        ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf, tot);
+    }
+    if (threadIdx.x == 0) {
+        sc.phase = 0;
+        sc.alpha = sc.beta = sc.delta = 0.0;
+        sc.restart = 1;
+        sc.bad = 0;
+        sc.refresh = 0;
+        sc.nr = 0.0;
+        sc.mu = tot[0];
+        sc.deflate = (tot[0] > 0.0 && isfinite(tot[0])) ? 1 : 0;
+    }
+    __syncthreads();
+    while (ok) {
+        // R1: FP64 true residual from x; 1.r for the coarse correction
+        double v2[2] = {0.0, 0.0};     // ||b||^2, 1.r
+        for (int i = i0; i < re; i += kCgBlock) {
+            const RowSpan rs = row_span(a.slice_ptr, i);
+            double ax = a.diag[i] * a.x[i];
+            for (int k = 0; k < rs.K; ++k) {
+                const int e = rs.e0 + 32 * k;
+                ax += a.val[e] * a.x[a.col[e]];
+            }
+            const double bi = a.b[i];
+            const double ri = bi - ax;
+            a.r64[i] = ri;
+            v2[0] += bi * bi;
+            v2[1] += ri;
+        }
+        if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
+        if (threadIdx.x == 0) {
+            if (outer == 0) sc.nb = sqrt(tot[0]);
+            sc.shift = sc.deflate ? tot[1] / sc.mu : 0.0;
+        }
+        __syncthreads();
+        // R2: coarse correction x += shift (r -= shift A 1), FP32 scaled residual
+        {
+            const double sh = sc.shift;
+            double v3[3] = {0.0, 0.0, 0.0};     // ||r||^2, r^.r^, v.r^
+            for (int i = i0; i < re; i += kCgBlock) {
+                const double ri = a.r64[i] - sh * a.a1[i];
+                a.x[i] += sh;
+                const float rh = (float)(a.s[i] * ri);
+                a.r[i] = rh;
+                a.e[i] = 0.0f;
+                v3[0] += ri * ri;
+                v3[1] += (double)rh * (double)rh;
+                v3[2] += (double)a.v[i] * (double)rh;
+            }
+            if (!(ok = cg_grid_sum<3>(v3, a.partA, a.bar, gen, a.spin, buf, tot))) break;
+        }
+        if (threadIdx.x == 0) {
+            const double prev = sc.nr;
+            sc.nr = sqrt(tot[0]);
+            if (outer == 0) {
+                sc.nr0 = sc.nr;
+                sc.thresh = fmax(a.tol * sc.nb, a.reltol * sc.nr0);
+                if (sc.nb == 0.0) sc.phase = 4;
+            } else if (sc.refresh == 2) {
+                sc.bad = (sc.nr >= prev) ? sc.bad + 1 : 0;
+                if (sc.bad >= 2) sc.phase = 3;
+            }
+            if (sc.phase == 0) {
+                if (!isfinite(sc.nr)) sc.phase = 3;
+                else if (sc.nr <= sc.thresh) sc.phase = 1;
+                else if (it >= a.maxit) sc.phase = 2;
+            }
+            // continue CG with the refreshed residual (van der Vorst - Ye)
+            sc.beta = (outer > 0 && sc.restart == 0 && sc.rho > 0.0) ? tot[1] / sc.rho : 0.0;
+            sc.rho = tot[1];
+            sc.rho_ref = tot[1];
+            sc.ratio = tot[1] > 0.0 ? sc.nr / sqrt(tot[1]) : 0.0;
+            sc.delta = sc.deflate ? tot[2] / sc.mu : 0.0;
+            sc.alpha = 0.0;          // the correction was folded into x
+            sc.refresh = 0;
+        }
+        __syncthreads();
+        ++outer;
+        if (sc.phase != 0) break;
+        // FP32 CG iterations until the next refresh
+        while (true) {
+            ++it;
+            const float alpha = (float)sc.alpha, beta = (float)sc.beta, delta = (float)sc.delta;
+            if (sc.restart) {
+                for (int i = i0; i < re; i += kCgBlock) a.p[i] = fmaf(-delta, a.w[i], a.r[i]);
+            } else {
+#pragma unroll 2
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const float po = a.p[i];
+                    a.e[i] = fmaf(alpha, po, a.e[i]);
+                    a.p[i] = fmaf(-delta, a.w[i], fmaf(beta, po, a.r[i]));
+                }
+            }
+            if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+            float pq32 = 0.0f;
+#pragma unroll 2
+            for (int i = i0; i < re; i += kCgBlock) {
+                const RowSpan rs = row_span(a.slice_ptr, i);
+                const float pi = a.p[i];
+                const float acc = spmv32_unit_row(a, rs, pi);
+                a.q[i] = acc;
+                pq32 = fmaf(pi, acc, pq32);
+            }
+            double v1[1] = {(double)pq32};
+            if (!(ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                sc.restart = 0;
+                const double pq = tot[0];
+                if (!(pq > 0.0) || !isfinite(pq)) { sc.refresh = 2; sc.alpha = 0.0; }
+                else sc.alpha = sc.rho / pq;
+            }
+            __syncthreads();
+            if (sc.refresh == 2) break;
+            const float al = (float)sc.alpha;
+            float rr32 = 0.0f, vr32 = 0.0f;
+#pragma unroll 2
+            for (int i = i0; i < re; i += kCgBlock) {
+                const float ri = fmaf(-al, a.q[i], a.r[i]);
+                a.r[i] = ri;
+                rr32 = fmaf(ri, ri, rr32);
+                vr32 = fmaf(a.v[i], ri, vr32);
+            }
+            double v2[2] = {(double)rr32, (double)vr32};
+            if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                const double rn = tot[0];
+                if (!isfinite(rn)) { sc.refresh = 2; }
+                else if (rn <= kReliable * kReliable * sc.rho_ref ||
+                         sc.ratio * sqrt(rn) <= sc.thresh || it >= a.maxit) {
+                    // refresh; sc.rho keeps r.r of the previous iteration so
+                    // that beta can be formed with the refreshed residual
+                    sc.refresh = 1;
+                } else {
+                    sc.beta = rn / sc.rho;
+                    sc.rho = rn;
+                    sc.delta = sc.deflate ? tot[1] / sc.mu : 0.0;
+                }
+            }
+            __syncthreads();
+            if (sc.refresh) break;
+        }
+        if (!ok) break;
+        // fold the FP32 correction (with the last step) into the FP64 solution
+        {
+            const float al = (float)sc.alpha;
+            for (int i = i0; i < re; i += kCgBlock) {
+                const float ei = fmaf(al, a.p[i], a.e[i]);
+                a.x[i] += a.s[i] * (double)ei;
+            }
+        }
+        if (threadIdx.x == 0 && sc.refresh == 2) sc.restart = 1;
+        __syncthreads();
+        if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+    }
+    if (ok && sc.phase == 4)
+        for (int i = i0; i < re; i += kCgBlock) a.x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int ph = sc.phase;
+        a.stats->iters = it;
+        a.stats->status = !ok ? FV_E_TIMEOUT
+                        : ph == 3 ? FV_E_DIVERGED : ph == 2 ? FV_E_NOT_CONVERGED : FV_OK;
+        const bool zero = ph == 4;
+        a.stats->res0 = zero ? 0.0 : sc.nr0 / sc.nb;
+        a.stats->res = zero ? 0.0 : sc.nr / sc.nb;
+        a.stats->outer = outer;
     }
 }
 
@@ -575,6 +853,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
             a.stats[c].status = ok ? status[c] : FV_E_TIMEOUT;
             a.stats[c].res0 = nb[c] > 0.0 ? nr0[c] / nb[c] : 0.0;
             a.stats[c].res = nb[c] > 0.0 ? nr[c] / nb[c] : 0.0;
+            a.stats[c].outer = 1;
         }
     }
 }
@@ -612,6 +891,8 @@ fv_status krylov_setup(fv_mesh *m)
     int per_sm = 0;
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "CG kernel cannot be resident");
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed, kCgBlock, 0));
+    FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel cannot be resident");
     w.Gcg = m->sm_count;
     int per_sm2 = 0;
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_bicgstab, kBlock, 0));
@@ -666,6 +947,51 @@ fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb)
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
     void *args[] = {&a};
     return coop_launch((const void *)k_pcg, grid_for(m->N, kCgBlock, w.Gcg), kCgBlock, args,
+                       m->stream);
+}
+
+fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb)
+{
+    fv_mesh *mm = const_cast<fv_mesh *>(m);
+    KrylovWork &w = mm->kw;
+    if (!w.val32) {
+        // FP32 work space, allocated once per mesh on first use
+        DeviceArena &ar = mm->arena;
+        fv_status st;
+        if ((st = ar.alloc_n(&w.val32, (size_t)m->nnz)) != FV_OK) return st;
+        for (int k = 0; k < 6; ++k)
+            if ((st = ar.alloc_n(&w.f32[k], (size_t)m->N)) != FV_OK) return st;
+    }
+    MixArgs a;
+    a.N = m->N;
+    a.slice_ptr = m->slice_ptr;
+    a.col = m->col;
+    a.val = pb.val;
+    a.val32 = w.val32;
+    a.diag = pb.diag;
+    a.b = pb.b;
+    a.x = pb.x;
+    a.s = w.dinv;
+    a.r64 = w.r;
+    a.a1 = w.y;
+    a.r = w.f32[0];
+    a.p = w.f32[1];
+    a.q = w.f32[2];
+    a.e = w.f32[3];
+    a.w = w.f32[4];
+    a.v = w.f32[5];
+    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
+    a.partA = w.partials;
+    a.partB = w.partials + (size_t)gp * kParts;
+    a.bar = w.bar;
+    a.spin = g_spin_limit;
+    a.tol = pb.tol;
+    a.reltol = pb.reltol;
+    a.maxit = pb.maxit;
+    a.stats = pb.stats;
+    FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
+    void *args[] = {&a};
+    return coop_launch((const void *)k_pcg_mixed, grid_for(m->N, kCgBlock, w.Gcg), kCgBlock, args,
                        m->stream);
 }
 

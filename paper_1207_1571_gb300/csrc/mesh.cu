@@ -10,6 +10,7 @@
 // boundary faces use d = Cf - C_P and carry no k.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -33,9 +34,24 @@ fv_status cuda_status(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? FV_E_NOMEM : FV_E_CUDA;
 }
 
+// Fault injection for tests: FVGB_FAIL_ALLOC_AFTER=k makes the (k+1)-th
+// device allocation of the process fail with FV_E_NOMEM (host-side only).
+static long long alloc_budget()
+{
+    static long long left = [] {
+        const char *e = getenv("FVGB_FAIL_ALLOC_AFTER");
+        return e ? atoll(e) : -1LL;
+    }();
+    return left < 0 ? 1 : left--;
+}
+
 fv_status DeviceArena::alloc(void **p, size_t n)
 {
     *p = nullptr;
+    if (alloc_budget() == 0) {
+        set_error("device allocation refused (FVGB_FAIL_ALLOC_AFTER)");
+        return FV_E_NOMEM;
+    }
     if (n == 0) n = 16;
     n = (n + 255) & ~size_t(255);
     cudaError_t e = cudaMalloc(p, n);
@@ -167,11 +183,16 @@ fv_status upload_mesh(fv_mesh *m, const fv_mesh_desc *d)
     }
     UP(m->Sf, Sf.data(), Sf.size());
     UP(m->V, V.data(), V.size());
+    // temporaries of the geometry kernel, freed when this function returns
+    struct Tmp {
+        DeviceArena a;
+        ~Tmp() { a.release(); }
+    } tmp;
     double *dCf = nullptr, *dC = nullptr;
     int *dflag = nullptr;
-    FV_CUDA(cudaMalloc(&dCf, sizeof(double) * Cf.size() + 16));
-    FV_CUDA(cudaMalloc(&dC, sizeof(double) * C.size() + 16));
-    FV_CUDA(cudaMalloc(&dflag, sizeof(int)));
+    if ((st = tmp.a.alloc_n(&dCf, Cf.size())) != FV_OK) return st;
+    if ((st = tmp.a.alloc_n(&dC, C.size())) != FV_OK) return st;
+    if ((st = tmp.a.alloc_n(&dflag, 1)) != FV_OK) return st;
     FV_CUDA(cudaMemcpyAsync(dCf, Cf.data(), sizeof(double) * Cf.size(), cudaMemcpyHostToDevice, s));
     FV_CUDA(cudaMemcpyAsync(dC, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, s));
     FV_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), s));
@@ -190,9 +211,6 @@ fv_status upload_mesh(fv_mesh *m, const fv_mesh_desc *d)
     FV_CUDA(cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     FV_CUDA(cudaStreamSynchronize(s));
     m->nonorth = flag;
-    cudaFree(dCf);
-    cudaFree(dC);
-    cudaFree(dflag);
     return FV_OK;
 }
 

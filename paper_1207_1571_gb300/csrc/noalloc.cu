@@ -97,6 +97,8 @@ extern "C" fv_status fv_pcg_solve_noalloc(const fv_mesh *mc, const double *diag,
         stats->status = h.status;
         stats->res0 = h.res0;
         stats->res = h.res;
+        stats->outer = h.outer;
+        stats->pad_ = 0;
     }
     return (fv_status)h.status;
 }

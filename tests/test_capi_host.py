@@ -44,8 +44,8 @@ def test_struct_sizes_match_header(P):
     import ctypes as C
     assert C.sizeof(_capi.fv_patch) == 48
     assert C.sizeof(_capi.fv_mesh_desc) == 80
-    assert C.sizeof(_capi.fv_solve_stats) == 24
-    assert C.sizeof(_capi.fv_step_stats) == 24 * 11 + 16
+    assert C.sizeof(_capi.fv_solve_stats) == 32
+    assert C.sizeof(_capi.fv_step_stats) == 32 * 11 + 16
     assert C.sizeof(_capi.fv_piso_params) == 48
     assert C.sizeof(_capi.fv_simple_params) == 72
     assert C.sizeof(_capi.fv_pcg_params) == 24

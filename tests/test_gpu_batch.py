@@ -1,0 +1,118 @@
+"""Batched cases (many independent 2-D cavities advanced by one launch per
+PISO stage) against the FP64 oracle, case by case."""
+import numpy as np
+import pytest
+
+import meshgen as mg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1207_1571_gb300 import build as B
+    B.build()
+    import paper_1207_1571_gb300 as P
+    P.load()
+    return P
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+def _cases():
+    # a small sample of the batch sampler's range: sizes 8..24, Re 10..1000
+    spec = [(8, 0.1), (24, 0.001), (13, 0.01), (20, 0.002), (9, 0.05), (17, 0.0015)]
+    return [(mg.cavity2d(n), nu) for n, nu in spec]
+
+
+def test_batch_matches_oracle_case_by_case(P):
+    cases = _cases()
+    bt = P.Batch([m for m, _ in cases], [nu for _, nu in cases], [m.corner_cell for m, _ in cases])
+    ocs = [O.Case(O.Mesh(m, renumber=True), nu) for m, nu in cases]
+    for step in range(12):
+        st = bt.piso_step(0.002, 2)
+        for k, oc in enumerate(ocs):
+            so = oc.piso_step(0.002, 2, p_ref_cell=cases[k][0].corner_cell)
+            gi, oi = np.array(st[k]["iters"]), so["iters"]
+            assert st[k]["status"] == 0
+            assert np.abs(gi - oi).max() <= 1, (step, k, gi, oi)
+    for k, oc in enumerate(ocs):
+        g = bt.get_fields(k)
+        o = oc.get_fields()
+        for a, b, name in zip(g, o, ("u", "p", "phi")):
+            assert rel(a, b) <= 1e-9, (k, name, rel(a, b))
+
+
+def test_batch_graph_and_schedules(P):
+    cases = _cases()
+    ms = [m for m, _ in cases]
+    nus = [nu for _, nu in cases]
+    refs = [m.corner_cell for m in ms]
+    a = P.Batch(ms, nus, refs)
+    for _ in range(5):
+        a.piso_step(0.002, 2, stats=False)
+    b = P.Batch(ms, nus, refs)
+    b.run_graph(5, 0.002, 2)
+    for k in range(len(ms)):
+        for x, y in zip(a.get_fields(k), b.get_fields(k)):
+            assert np.array_equal(x, y)
+    # every schedule solves the same problem (summation order differs)
+    ref_fields = [a.get_fields(k) for k in range(len(ms))]
+    for sched in range(len(P.Batch.schedules())):
+        c = P.Batch(ms, nus, refs)
+        c.set_schedule(sched)
+        for _ in range(5):
+            c.piso_step(0.002, 2, stats=False)
+        for k in range(len(ms)):
+            for x, y in zip(c.get_fields(k), ref_fields[k]):
+                assert rel(x, y) <= 1e-9
+    tuned = b.autotune(0.002, 2)
+    assert 0 <= tuned["schedule"] < len(P.Batch.schedules()) and len(tuned["ms"]) >= 4
+
+
+def test_batch_sampler_subset(P):
+    """Eight cases drawn by the batch sampler itself (seed 7), five steps."""
+    spec = mg.batch_cases()[:8]
+    ms = [mg.cavity2d(n) for n, _ in spec]
+    nus = [nu for _, nu in spec]
+    bt = P.Batch(ms, nus, [m.corner_cell for m in ms])
+    ocs = [O.Case(O.Mesh(m, renumber=True), nu) for m, nu in zip(ms, nus)]
+    for _ in range(5):
+        st = bt.piso_step(0.002, 2)
+        for k, oc in enumerate(ocs):
+            so = oc.piso_step(0.002, 2, p_ref_cell=ms[k].corner_cell)
+            assert np.abs(np.array(st[k]["iters"]) - so["iters"]).max() <= 1
+    for k, oc in enumerate(ocs):
+        for a, b in zip(bt.get_fields(k), oc.get_fields()):
+            assert rel(a, b) <= 1e-9
+
+
+def test_batch_mixed_precision_against_fp64_oracle(P):
+    """Batched cases with the mixed-precision pressure solve: every solve
+    meets the FP64 tolerance on its true residual; fields stay within the
+    solver tolerance of the FP64 oracle."""
+    import paper_1207_1571_gb300 as PP
+    cases = _cases()
+    ms = [m for m, _ in cases]
+    nus = [nu for _, nu in cases]
+    bt = P.Batch(ms, nus, [m.corner_cell for m in ms], PP.FV_PREC_MIXED)
+    ocs = [O.Case(O.Mesh(m, renumber=True), nu) for m, nu in cases]
+    for _ in range(10):
+        st = bt.piso_step(0.002, 2)
+        for k, oc in enumerate(ocs):
+            oc.piso_step(0.002, 2, p_ref_cell=ms[k].corner_cell)
+            assert st[k]["status"] == 0
+            assert all(sp["res"] <= 1e-6 for sp in st[k]["p"])
+    for k, oc in enumerate(ocs):
+        u, p, phi = bt.get_fields(k)
+        uo, po, phio = oc.get_fields()
+        assert rel(u, uo) < 1e-5 and rel(phi, phio) < 1e-5, (k, rel(u, uo), rel(phi, phio))
+        # pressure up to the constant the reference pin fixes only weakly
+        assert rel(p - p.mean(), po - po.mean()) < 1e-4, (k, rel(p, po))
