@@ -253,8 +253,10 @@ fv_status fv_batch_run_graph(fv_batch *bt, const fv_piso_params *prm, int32_t n_
 fv_status fv_batch_get_fields(const fv_batch *bt, int32_t c, double *u, double *p, double *phi);
 /* Schedules of the per-case Krylov kernels: info = {threads per block, rows
  * per thread per loop trip, block reduction (0 shuffle tree, 1 shared-memory
- * staging), number of schedules}. */
-fv_status fv_batch_schedule_info(int32_t schedule, int32_t *info /* host [4] */);
+ * staging), number of schedules, blocks per case in the pressure solve (a
+ * thread-block cluster sharing the case through distributed shared
+ * memory)}. */
+fv_status fv_batch_schedule_info(int32_t schedule, int32_t *info /* host [5] */);
 fv_status fv_batch_set_schedule(fv_batch *bt, int32_t schedule);
 /* Autotuner: time one PISO step with every schedule from the current state
  * (restored after each trial), keep the fastest; best (host, may be NULL)

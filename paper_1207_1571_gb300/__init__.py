@@ -391,12 +391,13 @@ class Batch:
     @staticmethod
     def schedules():
         L = load()
-        a = np.zeros(4, np.int32)
+        a = np.zeros(5, np.int32)
         check(L.fv_batch_schedule_info(0, a.ctypes.data), "fv_batch_schedule_info")
         out = []
         for k in range(int(a[3])):
             check(L.fv_batch_schedule_info(k, a.ctypes.data), "fv_batch_schedule_info")
-            out.append(dict(block=int(a[0]), rows_per_trip=int(a[1]), reduction=int(a[2])))
+            out.append(dict(block=int(a[0]), rows_per_trip=int(a[1]), reduction=int(a[2]),
+                            blocks_per_case=int(a[4])))
         return out
 
     def set_schedule(self, k: int):

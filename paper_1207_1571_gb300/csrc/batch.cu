@@ -21,6 +21,8 @@
 #include <numeric>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "fvgb_internal.h"
 
 struct fv_batch {
@@ -46,11 +48,17 @@ constexpr int kStatStride = 3 + FV_MAX_CORR;
 
 // ------------------------------------------------------------ schedules --
 
+// block = threads per block, unroll = rows per thread per loop trip,
+// red = block reduction (0 shuffle tree, 1 shared-memory staging),
+// cl = blocks per case for the pressure solve (a thread-block cluster
+// sharing one case through distributed shared memory; the momentum solve
+// always uses one block of at most 512 threads per case).
 struct Sched {
-    int block, unroll, red;
+    int block, unroll, red, cl;
 };
-constexpr Sched kScheds[] = {{128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {256, 2, 0}, {256, 1, 1},
-                             {256, 2, 1}, {512, 1, 0}, {512, 2, 1}};
+constexpr Sched kScheds[] = {{256, 2, 0, 1},  {256, 2, 1, 1},  {512, 1, 1, 1},  {512, 2, 1, 1},
+                             {1024, 2, 1, 1}, {512, 2, 1, 2},  {1024, 2, 1, 2}, {512, 2, 1, 4},
+                             {1024, 2, 1, 4}, {1024, 2, 1, 8}};
 constexpr int kNSched = sizeof(kScheds) / sizeof(kScheds[0]);
 
 // Block sum; result in tot[] (shared), visible to all threads on return.
@@ -132,6 +140,50 @@ __device__ __forceinline__ int next_case(int32_t *counter, int *slot)
     return q;
 }
 
+// ---------------------------------------------------- cluster helpers ----
+// A case of the pressure solve is owned by a cluster of CL blocks (CL = 1:
+// one block).  Phases are separated by a cluster barrier (release/acquire at
+// cluster scope, so rows written by one block are visible to the others);
+// reductions add the CL block totals, read through distributed shared
+// memory in rank order, so every block holds the same bits.
+
+template <int CL>
+__device__ __forceinline__ void csync()
+{
+    if (CL == 1) __syncthreads();
+    else cooperative_groups::this_cluster().sync();
+}
+
+template <int BLOCK, int RED, int CL, int NV>
+__device__ __forceinline__ void csum(double (&v)[NV], double *tot, double *cpart, int &par)
+{
+    bsum<BLOCK, RED, NV>(v, tot);
+    if (CL == 1) return;
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    if (threadIdx.x < NV) cpart[par * 8 + threadIdx.x] = tot[threadIdx.x];
+    cl.sync();
+    if (threadIdx.x < NV) {
+        double x = 0.0;
+        for (int r = 0; r < CL; ++r) x += cl.map_shared_rank(cpart, r)[par * 8 + threadIdx.x];
+        tot[threadIdx.x] = x;
+    }
+    par ^= 1;    // the next reduction uses the other half (see the barrier argument above)
+    __syncthreads();
+}
+
+// next case for the cluster: rank 0 takes it from the queue
+template <int CL>
+__device__ __forceinline__ int cluster_next_case(int32_t *counter, int *slot)
+{
+    if (CL == 1) return next_case(counter, slot);
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    if (cl.block_rank() == 0 && threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+    cl.sync();
+    const int q = *cl.map_shared_rank(slot, 0);
+    cl.sync();
+    return q;
+}
+
 // --------------------------------------------------------------- CG ----
 
 struct BCg {
@@ -147,18 +199,22 @@ struct BCg {
     DevSolveStats *stats;     // + case * kStatStride
 };
 
-template <int BLOCK, int U, int RED>
+template <int BLOCK, int U, int RED, int CL>
 __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
 {
     __shared__ int slot;
-    __shared__ double tot[3];
+    __shared__ double tot[3], cpart[16];
     __shared__ double sc_alpha, sc_beta, sc_rho, sc_thr, sc_nb, sc_nr0, sc_nr;
     __shared__ int sc_phase;
+    const int rank = CL == 1 ? 0 : (int)cooperative_groups::this_cluster().block_rank();
+    int par = 0;
     for (;;) {
-        const int q = next_case(a.next, &slot);
+        const int q = cluster_next_case<CL>(a.next, &slot);
         if (q >= a.ncase) break;
         const int cid = a.order[q];
-        const int r0 = a.start[cid], r1 = r0 + a.count[cid];
+        const int n = a.count[cid], chunk = (n + CL - 1) / CL;
+        const int r0 = a.start[cid] + min(n, rank * chunk);
+        const int r1 = a.start[cid] + min(n, (rank + 1) * chunk);
         const int i0 = r0 + threadIdx.x;
         int it = 0;
         for (int i = i0; i < r1; i += BLOCK) {
@@ -166,7 +222,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
             a.s[i] = 1.0 / sq;
             a.y[i] = a.x[i] * sq;
         }
-        __syncthreads();
+        csync<CL>();
         {
             double v3[3] = {0.0, 0.0, 0.0};
             for (int i = i0; i < r1; i += BLOCK) {
@@ -187,7 +243,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
                 v3[1] += d * rh * rh;
                 v3[2] += rh * rh;
             }
-            bsum<BLOCK, RED, 3>(v3, tot);
+            csum<BLOCK, RED, CL, 3>(v3, tot, cpart, par);
         }
         if (threadIdx.x == 0) {
             sc_nb = sqrt(tot[0]);
@@ -214,7 +270,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
                         a.p[i] = a.r[i] + be * po;
                     }
                 }
-                __syncthreads();
+                csync<CL>();
                 double v1[1] = {0.0};
 #pragma unroll U
                 for (int i = i0; i < r1; i += BLOCK) {
@@ -228,7 +284,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
                     a.q[i] = acc;
                     v1[0] += pi * acc;
                 }
-                bsum<BLOCK, RED, 1>(v1, tot);
+                csum<BLOCK, RED, CL, 1>(v1, tot, cpart, par);
                 if (threadIdx.x == 0) {
                     const double pq = tot[0];
                     if (!(pq > 0.0) || !isfinite(pq)) { sc_phase = 3; sc_alpha = 0.0; }
@@ -246,7 +302,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
                     v2[0] += r2;
                     v2[1] += a.diag[i] * r2;
                 }
-                bsum<BLOCK, RED, 2>(v2, tot);
+                csum<BLOCK, RED, CL, 2>(v2, tot, cpart, par);
                 if (threadIdx.x == 0) {
                     sc_nr = sqrt(tot[1]);
                     if (!isfinite(sc_nr)) sc_phase = 3;
@@ -260,7 +316,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
             const double af = sc_phase == 3 ? 0.0 : sc_alpha;
             for (int i = i0; i < r1; i += BLOCK) a.x[i] = a.s[i] * (a.y[i] + af * a.p[i]);
         }
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && rank == 0) {
             DevSolveStats *st = a.stats + (size_t)cid * kStatStride;
             const int ph = sc_phase;
             st->iters = it;
@@ -295,23 +351,27 @@ struct BMix {
     DevSolveStats *stats;
 };
 
-template <int BLOCK, int U, int RED>
+template <int BLOCK, int U, int RED, int CL>
 __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
 {
     __shared__ int slot;
-    __shared__ double tot[3];
+    __shared__ double tot[3], cpart[16];
     __shared__ double s_nb, s_nr0, s_nr, s_thr, s_rho, s_ref, s_ratio, s_alpha, s_beta, s_mu,
         s_delta, s_shift;
     __shared__ int s_phase, s_refresh, s_restart, s_bad, s_defl;
+    const int rank = CL == 1 ? 0 : (int)cooperative_groups::this_cluster().block_rank();
+    int par = 0;
     for (;;) {
-        const int qq = next_case(a.next, &slot);
+        const int qq = cluster_next_case<CL>(a.next, &slot);
         if (qq >= a.ncase) break;
         const int cid = a.order[qq];
-        const int r0 = a.start[cid], r1 = r0 + a.count[cid];
+        const int n = a.count[cid], chunk = (n + CL - 1) / CL;
+        const int r0 = a.start[cid] + min(n, rank * chunk);
+        const int r1 = a.start[cid] + min(n, (rank + 1) * chunk);
         const int i0 = r0 + threadIdx.x;
         int it = 0, outer = 0;
         for (int i = i0; i < r1; i += BLOCK) a.s[i] = 1.0 / sqrt(a.diag[i]);
-        __syncthreads();
+        csync<CL>();
         {
             double v1[1] = {0.0};
             for (int i = i0; i < r1; i += BLOCK) {
@@ -329,7 +389,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
                 a.v[i] = (float)(si * row);
                 v1[0] += row;
             }
-            bsum<BLOCK, RED, 1>(v1, tot);
+            csum<BLOCK, RED, CL, 1>(v1, tot, cpart, par);
         }
         if (threadIdx.x == 0) {
             s_phase = 0; s_alpha = s_beta = s_delta = 0.0; s_restart = 1; s_bad = 0;
@@ -352,7 +412,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
                     v2[0] += bi * bi;
                     v2[1] += ri;
                 }
-                bsum<BLOCK, RED, 2>(v2, tot);
+                csum<BLOCK, RED, CL, 2>(v2, tot, cpart, par);
             }
             if (threadIdx.x == 0) {
                 if (outer == 0) s_nb = sqrt(tot[0]);
@@ -372,7 +432,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
                     v3[1] += (double)rh * (double)rh;
                     v3[2] += (double)a.v[i] * (double)rh;
                 }
-                bsum<BLOCK, RED, 3>(v3, tot);
+                csum<BLOCK, RED, CL, 3>(v3, tot, cpart, par);
             }
             if (threadIdx.x == 0) {
                 const double prev = s_nr;
@@ -413,7 +473,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
                         a.p[i] = fmaf(-de, a.w[i], fmaf(be, po, a.r[i]));
                     }
                 }
-                __syncthreads();
+                csync<CL>();
                 float pq32 = 0.0f;
 #pragma unroll U
                 for (int i = i0; i < r1; i += BLOCK) {
@@ -428,7 +488,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
                     pq32 = fmaf(pi, acc, pq32);
                 }
                 double v1[1] = {(double)pq32};
-                bsum<BLOCK, RED, 1>(v1, tot);
+                csum<BLOCK, RED, CL, 1>(v1, tot, cpart, par);
                 if (threadIdx.x == 0) {
                     s_restart = 0;
                     const double pq = tot[0];
@@ -447,7 +507,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
                     vr32 = fmaf(a.v[i], ri, vr32);
                 }
                 double v2[2] = {(double)rr32, (double)vr32};
-                bsum<BLOCK, RED, 2>(v2, tot);
+                csum<BLOCK, RED, CL, 2>(v2, tot, cpart, par);
                 if (threadIdx.x == 0) {
                     const double rn = tot[0];
                     if (!isfinite(rn)) s_refresh = 2;
@@ -466,11 +526,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_mixed_batch(BMix a)
             const float a32 = (float)s_alpha;
             for (int i = i0; i < r1; i += BLOCK) a.x[i] += a.s[i] * (double)fmaf(a32, a.p[i], a.e[i]);
             if (threadIdx.x == 0 && s_refresh == 2) s_restart = 1;
-            __syncthreads();
+            csync<CL>();
         }
         if (s_phase == 4)
             for (int i = i0; i < r1; i += BLOCK) a.x[i] = 0.0;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && rank == 0) {
             DevSolveStats *st = a.stats + (size_t)cid * kStatStride;
             const int ph = s_phase;
             st->iters = it;
@@ -680,34 +740,51 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
 
 // ------------------------------------------------------------ launches --
 
-template <int BLOCK, int U, int RED>
+template <int BLOCK, int U, int RED, int CL>
 fv_status launch_batch_solvers(fv_batch *bt, int which, const void *argp)
 {
     const fv_mesh *m = bt->mesh;
+    constexpr int BB = BLOCK < 512 ? BLOCK : 512;      // momentum solve: one block per case
+    const void *fn = which == 0 ? (const void *)k_bicgstab_batch<BB, U, RED>
+                   : which == 1 ? (const void *)k_pcg_batch<BLOCK, U, RED, CL>
+                                : (const void *)k_pcg_mixed_batch<BLOCK, U, RED, CL>;
+    const int block = which == 0 ? BB : BLOCK;
+    const int cl = which == 0 ? 1 : CL;
     int per_sm = 0;
-    const void *fn = which == 0 ? (const void *)k_bicgstab_batch<BLOCK, U, RED>
-                   : which == 1 ? (const void *)k_pcg_batch<BLOCK, U, RED>
-                                : (const void *)k_pcg_mixed_batch<BLOCK, U, RED>;
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BLOCK, 0));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
     if (per_sm < 1) per_sm = 1;
-    int G = m->sm_count * per_sm;
-    if (G > bt->ncase) G = bt->ncase;
+    int groups = m->sm_count * per_sm / cl;
+    if (groups > bt->ncase) groups = bt->ncase;
+    if (groups < 1) groups = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(groups * cl);
+    cfg.blockDim = dim3(block);
+    cfg.stream = m->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     void *args[] = {const_cast<void *>(argp)};
-    FV_CUDA(cudaLaunchKernel(fn, dim3(G), dim3(BLOCK), args, 0, m->stream));
+    FV_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
     return FV_OK;
 }
 
 fv_status dispatch(fv_batch *bt, int which, const void *argp)
 {
     switch (bt->cfg) {
-    case 0: return launch_batch_solvers<128, 1, 0>(bt, which, argp);
-    case 1: return launch_batch_solvers<128, 2, 0>(bt, which, argp);
-    case 2: return launch_batch_solvers<256, 1, 0>(bt, which, argp);
-    case 3: return launch_batch_solvers<256, 2, 0>(bt, which, argp);
-    case 4: return launch_batch_solvers<256, 1, 1>(bt, which, argp);
-    case 5: return launch_batch_solvers<256, 2, 1>(bt, which, argp);
-    case 6: return launch_batch_solvers<512, 1, 0>(bt, which, argp);
-    default: return launch_batch_solvers<512, 2, 1>(bt, which, argp);
+    case 0: return launch_batch_solvers<256, 2, 0, 1>(bt, which, argp);
+    case 1: return launch_batch_solvers<256, 2, 1, 1>(bt, which, argp);
+    case 2: return launch_batch_solvers<512, 1, 1, 1>(bt, which, argp);
+    case 3: return launch_batch_solvers<512, 2, 1, 1>(bt, which, argp);
+    case 4: return launch_batch_solvers<1024, 2, 1, 1>(bt, which, argp);
+    case 5: return launch_batch_solvers<512, 2, 1, 2>(bt, which, argp);
+    case 6: return launch_batch_solvers<1024, 2, 1, 2>(bt, which, argp);
+    case 7: return launch_batch_solvers<512, 2, 1, 4>(bt, which, argp);
+    case 8: return launch_batch_solvers<1024, 2, 1, 4>(bt, which, argp);
+    default: return launch_batch_solvers<1024, 2, 1, 8>(bt, which, argp);
     }
 }
 
@@ -1039,7 +1116,7 @@ extern "C" fv_status fv_batch_create(const fv_mesh_desc *descs, int32_t n, const
         if (e == cudaSuccess) e = cudaMemsetAsync(bt->d_stats, 0, sizeof(DevSolveStats) * n * kStatStride, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { fv_batch_destroy(bt); return cuda_status(e, "batch upload"); }
-        bt->cfg = 2;   // 256 threads, one row per trip, shuffle reduction until tuned
+        bt->cfg = 3;   // 512 threads, two rows per trip, staged reduction until tuned
     } catch (const std::bad_alloc &) {
         fv_batch_destroy(bt);
         set_error("host allocation failed in fv_batch_create");
@@ -1128,6 +1205,7 @@ extern "C" fv_status fv_batch_schedule_info(int32_t schedule, int32_t *info)
     info[1] = kScheds[schedule].unroll;
     info[2] = kScheds[schedule].red;
     info[3] = kNSched;
+    info[4] = kScheds[schedule].cl;
     return FV_OK;
 }
 
