@@ -18,6 +18,7 @@ instead (a bounded sample of the same workload, see ``REF_SAMPLE``).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -41,6 +42,8 @@ WORKLOADS = {
     "cavity3d_200": dict(n=200, dim=3, nu=0.01, dt=0.001, n_corr=2, seed=1234),
     "cavity3d_40": dict(n=40, dim=3, nu=0.01, dt=0.002, n_corr=2, seed=1234),
     "cavity2d_20": dict(n=20, dim=2, nu=0.1, dt=0.005, n_corr=2, seed=None),
+    # transient Poiseuille flow, 3200 x 300 2-D pipe, inlet 0.01 sin(pi t)
+    "tp1M": dict(tp=True, nu=3.3e-6, dt=1e-4, n_corr=2),
     "batch256": dict(batch=True),
 }
 # bounded sample of the cavity used for the CPU reference arm
@@ -63,12 +66,44 @@ def peaks():
 
 def make_mesh(w):
     import meshgen as mg
+    if w.get("tp"):
+        return mg.tp_channel()
     if w["dim"] == 2:
         return mg.cavity2d(w["n"])
     m = mg.cavity3d(w["n"])
     if w["seed"] is not None:
         m = mg.permute_cells(m, mg.random_permutation(m.n_cells, w["seed"]))
     return m
+
+
+def ref_cell(w, m):
+    """Pressure reference: the corner cell of a closed cavity; none when an
+    outlet fixes p."""
+    return -1 if w.get("tp") else m.corner_cell
+
+
+def set_bc(L, case_h, w, m, k):
+    """Time-dependent boundary values before step k (0-based, from rest):
+    the tp1M inlet at the new time level (k + 1) dt."""
+    if not w.get("tp"):
+        return
+    import meshgen as mg
+    u = (ctypes.c_double * 3)(*mg.tp_inlet((k + 1) * w["dt"]))
+    _check_rc(L.fv_patch_set_value(case_h, m.patch("inlet"), u, 0.0), "fv_patch_set_value")
+
+
+def _check_rc(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with status {rc}")
+
+
+def workload_name(name, w, m):
+    if w.get("tp"):
+        return (f"{name}: transient Poiseuille flow, 2-D pipe 0.16 x 0.02 m, 3200 x 300 cells, "
+                "uniform inlet 0.01 sin(pi t) m/s, p = 0 outlet")
+    if w["dim"] == 3:
+        return f"{name}: 3-D lid-driven cavity {w['n']}^3 hex cells"
+    return f"{name}: 2-D lid-driven cavity"
 
 
 def cg_bytes_per_iter(N, F):
@@ -201,7 +236,7 @@ def run_ours(args, ws, rank, local):
     N, F = m.n_cells, m.n_internal_faces
     mesh = P.Mesh(m, renumber=True)
     case = P.Case(mesh, w["nu"])
-    ref = m.corner_cell
+    ref = ref_cell(w, m)
     prm = case.piso_params(w["dt"], w["n_corr"], p_ref_cell=ref)
     stream = mesh.stream
     zero = (torch.zeros(3, N, dtype=torch.float64, device="cuda"),
@@ -209,13 +244,15 @@ def run_ours(args, ws, rank, local):
             torch.zeros(m.n_faces, dtype=torch.float64, device="cuda"))
     st = _capi.fv_step_stats()
 
-    def step(with_stats=True):
-        rc = L.fv_piso_step(case.h, C.byref(prm), C.byref(st) if with_stats else None)
+    def step(k, with_stats=True, h=None):
+        h = case.h if h is None else h
+        set_bc(L, h, w, m, k)
+        rc = L.fv_piso_step(h, C.byref(prm), C.byref(st) if with_stats else None)
         _capi.check(rc, "fv_piso_step", allow=(4,))
         return st
 
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        step(k)
     case.set_fields(*zero)
     torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -231,7 +268,7 @@ def run_ours(args, ws, rank, local):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 ev[k][0].record(stream)
-            step(with_stats=False)
+            step(k, with_stats=False)
             with torch.cuda.stream(stream):
                 ev[k][1].record(stream)
             # statistics of this step, read after its end event (synchronises)
@@ -270,8 +307,8 @@ def run_ours(args, ws, rank, local):
     if not args.no_mixed:
         cm = P.Case(mesh, w["nu"], P.FV_PREC_MIXED)
         stm = _capi.fv_step_stats()
-        for _ in range(args.warmup):
-            _capi.check(L.fv_piso_step(cm.h, C.byref(prm), C.byref(stm)), "fv_piso_step", allow=(4,))
+        for k in range(args.warmup):
+            step(k, h=cm.h)
         cm.set_fields(*zero)
         torch.cuda.synchronize()
         evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -283,7 +320,7 @@ def run_ours(args, ws, rank, local):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 evm[k][0].record(stream)
-            _capi.check(L.fv_piso_step(cm.h, C.byref(prm), None), "fv_piso_step")
+            step(k, with_stats=False, h=cm.h)
             with torch.cuda.stream(stream):
                 evm[k][1].record(stream)
             sm_ = cm.last_stats()
@@ -304,6 +341,8 @@ def run_ours(args, ws, rank, local):
                  "rel_l2_vs_fp64_gpu": {"u": d_(ub, ua), "p": d_(pb_, pa), "phi": d_(fb, fa)}}
         cm.close()
 
+    formats = None if args.no_formats else spmv_formats(P, mesh, m, stream)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -315,7 +354,7 @@ def run_ours(args, ws, rank, local):
             t0 = time.perf_counter()
             _capi.check(L.fv_case_set_fields_host(case.h, hu.ctypes.data, hp.ctypes.data,
                                                   hphi.ctypes.data, 1), "set_fields_host")
-            step(with_stats=False)
+            step(k, with_stats=False)
             _capi.check(L.fv_case_get_fields_host(case.h, hu.ctypes.data, hp.ctypes.data,
                                                   hphi.ctypes.data, 1), "get_fields_host")
             te += time.perf_counter() - t0
@@ -329,10 +368,11 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "steps_per_s": args.steps / t,
-        "config": {"workload": f"{args.workload}: 3-D lid-driven cavity {w['n']}^3 hex cells"
-                   if w["dim"] == 3 else f"{args.workload}: 2-D lid-driven cavity",
+        "config": {"workload": workload_name(args.workload, w, m),
                    "cells": N, "internal_faces": F, "nu": w["nu"], "dt": w["dt"],
-                   "n_corr": w["n_corr"], "p_tol": 1e-6, "renumbering": "seed-1234 permutation + RCM",
+                   "n_corr": w["n_corr"], "p_tol": 1e-6,
+                   "renumbering": "RCM" if w.get("tp") or w.get("seed") is None
+                   else f"seed-{w['seed']} permutation + RCM",
                    "l2": "flushed (256 MiB write) between timed steps; steps timed from rest",
                    "parallelism": "replicas only" if ws > 1 else "1 GPU"},
         "cg": {"iterations": iters_p, "iters_per_step": iters_p / args.steps,
@@ -354,6 +394,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clk_sum,
         "e2e": e2e,
         "mixed": mixed,
+        "spmv_formats": formats,
         "memory_bytes": case.memory_bytes(),
         "statuses": sorted(set(statuses)),
     }
@@ -364,12 +405,62 @@ def run_ours(args, ws, rank, local):
         errs = {}
         for name, prec in (("fp64", P.FV_PREC_FP64), ("mixed", P.FV_PREC_MIXED)):
             c1 = P.Case(mesh, w["nu"], prec)
-            c1.piso_step(w["dt"], w["n_corr"], p_ref_cell=ref)
+            step(0, h=c1.h)
             g = c1.get_fields_host()
             errs[name] = {k: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
                           for k, a, b in zip(("u", "p", "phi"), g, ofields)}
             c1.close()
         out["first_step_rel_l2_vs_oracle"] = errs
+    return out
+
+
+def spmv_formats(P, mesh, m, stream, reps=20):
+    """One matrix-vector product in each storage, on the workload's mesh:
+    the LDU face arrays read through the SELL-32 rows (fv_ldu_matvec), and
+    the paper's hybrid ELL + J storage by rows (SMVP) and by columns
+    (STMVP, through I and J or the packed Q).  Mean device time of `reps`
+    products after one warm-up, CUDA events on the library stream; GB/s
+    from the arrays each product reads and writes once."""
+    import torch
+    N, F = m.n_cells, m.n_internal_faces
+    g = torch.Generator(device="cuda").manual_seed(3)
+    d = torch.rand(N, dtype=torch.float64, device="cuda", generator=g) + 4
+    up = torch.randn(F, dtype=torch.float64, device="cuda", generator=g)
+    lo = torch.randn(F, dtype=torch.float64, device="cuda", generator=g)
+    x = torch.randn(N, dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    e = P.Ellj(mesh)
+    V, Cv = e.from_ldu(d, up, lo)
+    L = mesh.L
+    nnz = N + 2 * F
+    K = e.K
+    ops = {
+        "ldu_sell32": (lambda: L.fv_ldu_matvec(mesh.h, d.data_ptr(), up.data_ptr(), lo.data_ptr(),
+                                               x.data_ptr(), y.data_ptr()),
+                       8 * N + 16 * F + 8 * 2 * F + 16 * N),
+        "ellj_smvp": (lambda: L.fv_ellj_spmv(e.h, V.data_ptr(), Cv.data_ptr(), x.data_ptr(),
+                                             y.data_ptr(), 0), 12 * K * N + 16 * N),
+        "ellj_stmvp": (lambda: L.fv_ellj_spmv(e.h, V.data_ptr(), Cv.data_ptr(), x.data_ptr(),
+                                              y.data_ptr(), 1), 16 * K * N + 16 * N),
+    }
+    if e.n_crs == 0:
+        ops["ellj_stmvp_q"] = (lambda: L.fv_ellj_spmv(e.h, V.data_ptr(), Cv.data_ptr(), x.data_ptr(),
+                                                      y.data_ptr(), 2), 12 * K * N + 16 * N)
+    out = {"K": K, "n_crs": e.n_crs, "nnz": nnz}
+    torch.cuda.synchronize()
+    for name, (fn, nbytes) in ops.items():
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            rc = fn()
+            if rc != 0:
+                raise RuntimeError(f"{name} failed with status {rc}")
+        b.record(stream)
+        b.synchronize()
+        us = 1e3 * a.elapsed_time(b) / reps
+        out[name] = {"us": us, "gbs": nbytes / us / 1e3, "bytes": nbytes}
+    e.close()
     return out
 
 
@@ -382,7 +473,10 @@ def cpu_baseline(workload):
     om = O.Mesh(m, renumber=True)
     oc = O.Case(om, w["nu"])
     t0 = time.perf_counter()
-    oc.piso_step(w["dt"], w["n_corr"], p_ref_cell=m.corner_cell)
+    if w.get("tp"):
+        import meshgen as mg
+        oc.set_patch(m.patch("inlet"), mg.tp_inlet(w["dt"]), 0.0)
+    oc.piso_step(w["dt"], w["n_corr"], p_ref_cell=ref_cell(w, m))
     t = time.perf_counter() - t0
     cb = {"value": m.n_cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
           "sample": f"1 PISO step from rest of {workload} ({m.n_cells} cells), "
@@ -528,6 +622,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-formats", action="store_true",
+                    help="skip the SpMV storage comparison (SELL-32 vs ELL + J)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="batch workload only")
     ap.add_argument("--schedule", type=int, default=None,

@@ -102,7 +102,8 @@ typedef struct {
 
 typedef struct {
     fv_solve_stats u[3];              /* momentum components */
-    fv_solve_stats p[FV_MAX_CORR];    /* pressure solves (n_corr for PISO, 1 for SIMPLE) */
+    fv_solve_stats p[FV_MAX_CORR];    /* pressure solves in order: corrector k, non-orthogonal
+                                         loop j at k (1 + n_nonorth) + j (PISO); loop j (SIMPLE) */
     int32_t n_p;
     int32_t status;                   /* worst status of the step */
     double init_res_max;              /* SIMPLE outer residual (see fv_simple_iter) */
@@ -118,6 +119,13 @@ typedef struct {
     int32_t p_ref_cell;    /* reference cell (caller's numbering) pinned to
                               p_ref_value when no outlet patch exists; -1 none */
     double p_ref_value;
+    int32_t n_nonorth;     /* non-orthogonal correctors: each pressure corrector
+                              solves 1 + n_nonorth times, the explicit
+                              non-orthogonal term re-evaluated from the newest
+                              pressure before each re-solve; the flux is
+                              corrected after the last.  0 = one solve.
+                              n_corr * (1 + n_nonorth) <= FV_MAX_CORR. */
+    int32_t pad_;
 } fv_piso_params;
 
 typedef struct {
@@ -126,7 +134,7 @@ typedef struct {
     double u_tol, u_reltol;    /* BiCGStab, same rule */
     int32_t p_maxit, u_maxit;
     int32_t p_ref_cell;        /* as in fv_piso_params */
-    int32_t pad_;
+    int32_t n_nonorth;         /* as in fv_piso_params; 1 + n_nonorth <= FV_MAX_CORR */
     double p_ref_value;
 } fv_simple_params;
 
@@ -190,7 +198,11 @@ fv_status fv_case_get_fields_host(const fv_case *cs, double *u, double *p, doubl
                                   int32_t original_order);
 
 /* Time-dependent boundary conditions (Sec. 1 and 6 of the paper): a uniform
- * value for patch q (u for fixed-velocity patches, p for outlets). */
+ * value for patch q (u for fixed-velocity patches, p for outlets); u NULL
+ * keeps the velocity values.  Stream-ordered and asynchronous (one small
+ * kernel on the mesh's stream, values passed by value): a value set between
+ * two enqueued steps applies from the second one, and the call may be
+ * captured in a CUDA graph.  Errors: FV_E_INVALID for a bad patch index. */
 fv_status fv_patch_set_value(fv_case *cs, int32_t q, const double u[3], double p);
 /* Per-face values for patch q in the caller's face order within the patch:
  * u host [3][size] (NULL keeps), p host [size] (NULL keeps). */
@@ -330,6 +342,50 @@ fv_status fv_gauss_grad(const fv_mesh *mesh, const double *x, const double *xb, 
  * mesh's internal order. */
 fv_status fv_ldu_matvec(const fv_mesh *mesh, const double *diag, const double *upper,
                         const double *lower, const double *x, double *y);
+
+/* ------------------------------------------- hybrid ELL + J storage -- */
+/* The paper's matrix storage (Sec. 3.1, its ELL / J / CRS example): the
+ * first K entries of each row (diagonal included, columns ascending) in ELL
+ * arrays V (values) and I (columns); the transpose-index array J, where
+ * J[i][k] is the ELL slot of the transposed entry A_ji in row j = I[i][k],
+ * so the same arrays can be read by columns (STMVP); the entries beyond the
+ * K-th of a row in CRS arrays.  The solver path does not use this storage
+ * (its SELL-32 rows are assembled from both sides of each face and never
+ * read by columns); it is provided for comparison.
+ * Encodings: empty ELL slot I = J = -1; a transposed entry in the CRS part
+ * at position p is named by -2 - p (in J and in crs_tr).  Without a CRS
+ * part, I and J are also packed as Q = K I + J (the paper's remark on
+ * combining them; its other formula, K J + I, is not decodable when I >= K,
+ * so K I + J is used). */
+typedef struct fv_ellj fv_ellj;
+
+/* Host only (no GPU): build the arrays for a structurally symmetric
+ * pattern given as row_ptr [n+1], col [row_ptr[n]] (columns strictly
+ * ascending per row).  Outputs are row-major n x K as in the paper: I, J
+ * [n*K]; crs_ptr [n+1]; crs_col, crs_tr [*n_crs].  With I == NULL only
+ * crs_ptr and *n_crs are produced (size query).  FV_E_INVALID: bad
+ * arguments, unsorted or out-of-range columns, an entry without transpose. */
+fv_status fv_ellj_build_host(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t K,
+                             int32_t *I, int32_t *J, int32_t *crs_ptr, int32_t *crs_col,
+                             int32_t *crs_tr, int32_t *n_crs);
+/* The storage of the mesh's LDU pattern (internal order) with width K
+ * (0 = the most frequent row length).  Index arrays are built on the host
+ * and copied to the device (synchronous); the library owns them. */
+fv_status fv_ellj_create(const fv_mesh *mesh, int32_t K, fv_ellj **out);
+fv_status fv_ellj_destroy(fv_ellj *ellj);
+/* K and the number of CRS entries (either pointer may be NULL). */
+fv_status fv_ellj_info(const fv_ellj *ellj, int32_t *K, int32_t *n_crs);
+/* Scatter an LDU matrix (diag [N], upper/lower [F], device, internal order)
+ * into V [K*N] (device, slot k of row i at k*N + i; empty slots set to 0)
+ * and C [n_crs] (device; may be NULL when n_crs == 0).  Asynchronous on the
+ * mesh's stream. */
+fv_status fv_ellj_from_ldu(const fv_ellj *ellj, const double *diag, const double *upper,
+                           const double *lower, double *V, double *C);
+/* y = A x (mode 0, by rows), y = A^T x (mode 1, by columns through I and
+ * J), or y = A^T x through the packed Q (mode 2; FV_E_UNSUPPORTED when the
+ * storage has a CRS part).  V, C, x, y: device; asynchronous. */
+fv_status fv_ellj_spmv(const fv_ellj *ellj, const double *V, const double *C, const double *x,
+                       double *y, int32_t mode);
 
 /* ---------------------------------------------------------- profiling -- */
 

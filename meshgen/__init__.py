@@ -212,6 +212,25 @@ def channel2d(nx: int, ny: int, Lx: float, Ly: float, inlet_u=(1.0, 0.0, 0.0),
     return hex_box(nx, ny, 1, (Lx, Ly, min(Lx / nx, Ly / ny)), sp, specs)
 
 
+# Transient Poiseuille flow (the paper's "tp1M" case, Sec. 4.1): a 2-D pipe
+# 0.16 m long and 0.02 m high, 3200 x 300 cells, nu = 3.3e-6 m^2/s, uniform
+# inlet velocity u0 sin(2 pi f t) with u0 = 0.01 m/s and f = 0.5 1/s, p = 0
+# at the outlet, 5000 PISO steps of 0.1 ms.
+TP1M = {"L": 0.16, "H": 0.02, "nx": 3200, "ny": 300, "nu": 3.3e-6, "u0": 0.01, "f": 0.5,
+        "dt": 1e-4, "steps": 5000}
+
+
+def tp_channel(nx: int = 3200, ny: int = 300, L: float = 0.16, H: float = 0.02) -> Mesh:
+    """The transient-Poiseuille pipe (inlet at x = 0, outlet at x = L, no-slip
+    walls at y = 0 and y = H); the inlet starts at rest."""
+    return channel2d(nx, ny, L, H, inlet_u=(0.0, 0.0, 0.0))
+
+
+def tp_inlet(t: float, u0: float = 0.01, f: float = 0.5) -> tuple:
+    """Inlet velocity of the transient-Poiseuille case at time t."""
+    return (u0 * float(np.sin(2.0 * np.pi * f * t)), 0.0, 0.0)
+
+
 # ---------------------------------------------------------------------------
 # Cell relabelling
 # ---------------------------------------------------------------------------

@@ -84,12 +84,13 @@ def lib():
             L.orc_case_state.argtypes = [vp, _f64p, _f64p, _f64p]
             L.orc_patch_set_value.argtypes = [vp, C.c_int, _f64p, C.c_double]
             L.orc_patch_set_face_values.argtypes = [vp, C.c_int, _f64p, vp]
-            L.orc_piso_step.argtypes = [vp, C.c_double, C.c_int, C.c_double, C.c_int, C.c_double,
-                                        C.c_int, C.c_int, C.c_double, _i32p, _f64p, dp]
+            L.orc_piso_step.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
+                                        C.c_double, C.c_int, C.c_int, C.c_double, _i32p, _f64p,
+                                        dp]
             L.orc_piso_step.restype = C.c_int
-            L.orc_simple_iter.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double,
-                                          C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
-                                          C.c_double, _i32p, _f64p, dp, dp]
+            L.orc_simple_iter.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                          C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
+                                          C.c_int, C.c_double, _i32p, _f64p, dp, dp]
             L.orc_simple_iter.restype = C.c_int
             L.orc_case_momentum_system.argtypes = [vp, C.c_int, C.c_double, C.c_double, _f64p,
                                                    _f64p, _f64p, _f64p]
@@ -97,6 +98,21 @@ def lib():
                                                    _f64p, _f64p]
             L.orc_case_grad_p.argtypes = [vp, _f64p]
             L.orc_laplacian_system.argtypes = [vp, _f64p, vp, _f64p, _f64p, _f64p]
+            L.orc_ellj_build.argtypes = [C.c_int, _i32p, _i32p, C.c_int, vp, vp, _i32p, vp, vp]
+            L.orc_ellj_build.restype = C.c_int
+            L.orc_amg_new.restype = vp
+            L.orc_amg_new.argtypes = [vp]
+            L.orc_amg_free.argtypes = [vp]
+            L.orc_amg_levels.argtypes = [vp, _i32p, _i32p]
+            L.orc_amg_levels.restype = C.c_int
+            L.orc_amg_maps.argtypes = [vp, C.c_int, _i32p, _i32p]
+            L.orc_amg_matrix.argtypes = [vp, C.c_int, _f64p, _f64p]
+            L.orc_amg_edges.argtypes = [vp, C.c_int, _i32p, _i32p]
+            L.orc_amg_vcycle.argtypes = [vp, _f64p, _f64p, _f64p, _f64p]
+            L.orc_amg_vcycle.restype = C.c_int
+            L.orc_amg_pcg.argtypes = [vp, _f64p, _f64p, _f64p, _f64p, C.c_double, C.c_double,
+                                      C.c_int, dp, dp, ip]
+            L.orc_amg_pcg.restype = C.c_int
             L.orc_gauss_grad.argtypes = [vp, _f64p, _f64p, _f64p]
             _lib = L
     return _lib
@@ -249,19 +265,22 @@ class Case:
         return self.get_fields(original_order=False)
 
     def piso_step(self, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10, u_maxit=1000,
-                  p_ref_cell=-1, p_ref=0.0):
-        ns = 3 + n_corr
+                  p_ref_cell=-1, p_ref=0.0, n_nonorth=0):
+        ns = 3 + n_corr * (n_nonorth + 1)
         its = np.zeros(ns, np.int32); res = np.zeros(2 * ns); ce = C.c_double()
-        st = lib().orc_piso_step(self.h, dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, p_ref_cell,
-                                 p_ref, its, res, C.byref(ce))
+        st = lib().orc_piso_step(self.h, dt, n_corr, n_nonorth, p_tol, p_maxit, u_tol, u_maxit,
+                                 p_ref_cell, p_ref, its, res, C.byref(ce))
         return dict(status=st, iters=its, res0=res[0::2], res=res[1::2], cont_err=ce.value)
 
     def simple_iter(self, alpha_u=0.7, alpha_p=0.3, p_tol=1e-10, p_reltol=0.01, p_maxit=10000,
-                    u_tol=1e-10, u_reltol=0.1, u_maxit=1000, p_ref_cell=-1, p_ref=0.0):
-        its = np.zeros(4, np.int32); res = np.zeros(8); ce = C.c_double(); irm = C.c_double()
-        st = lib().orc_simple_iter(self.h, alpha_u, alpha_p, p_tol, p_reltol, p_maxit, u_tol,
-                                   u_reltol, u_maxit, p_ref_cell, p_ref, its, res, C.byref(ce),
-                                   C.byref(irm))
+                    u_tol=1e-10, u_reltol=0.1, u_maxit=1000, p_ref_cell=-1, p_ref=0.0,
+                    n_nonorth=0):
+        ns = 4 + n_nonorth
+        its = np.zeros(ns, np.int32); res = np.zeros(2 * ns); ce = C.c_double()
+        irm = C.c_double()
+        st = lib().orc_simple_iter(self.h, alpha_u, alpha_p, n_nonorth, p_tol, p_reltol, p_maxit,
+                                   u_tol, u_reltol, u_maxit, p_ref_cell, p_ref, its, res,
+                                   C.byref(ce), C.byref(irm))
         return dict(status=st, iters=its, res0=res[0::2], res=res[1::2], cont_err=ce.value,
                     init_res_max=irm.value)
 
@@ -281,3 +300,91 @@ class Case:
         g = np.zeros(3 * self.mesh.N)
         lib().orc_case_grad_p(self.h, g)
         return g.reshape(3, self.mesh.N)
+
+
+def ellj_build(row_ptr, col, K):
+    """Hybrid ELL + J + CRS arrays of a structurally symmetric pattern (paper
+    Sec. 3.1): returns dict(I, J) as N x K arrays, crs_ptr, crs_col, crs_tr."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(row_ptr) - 1
+    crs_ptr = np.zeros(n + 1, np.int32)
+    ncrs = lib().orc_ellj_build(n, row_ptr, col, K, None, None, crs_ptr, None, None)
+    I = np.zeros((n, K), np.int32)
+    J = np.zeros((n, K), np.int32)
+    crs_col = np.zeros(max(ncrs, 1), np.int32)
+    crs_tr = np.zeros(max(ncrs, 1), np.int32)
+    rc = lib().orc_ellj_build(n, row_ptr, col, K, I.ctypes.data, J.ctypes.data, crs_ptr,
+                              crs_col.ctypes.data, crs_tr.ctypes.data)
+    if rc < 0:
+        raise ValueError("sparsity pattern is not structurally symmetric")
+    return dict(I=I, J=J, crs_ptr=crs_ptr, crs_col=crs_col[:ncrs], crs_tr=crs_tr[:ncrs])
+
+
+def pattern_rows(n, own, nei):
+    """Row structure of an LDU matrix (diagonal plus both sides of every
+    internal face), columns ascending: (row_ptr, col)."""
+    own = np.asarray(own[:len(nei)], dtype=np.int64)
+    nei = np.asarray(nei, dtype=np.int64)
+    r = np.concatenate([np.arange(n), own, nei])
+    c = np.concatenate([np.arange(n), nei, own])
+    order = np.lexsort((c, r))
+    r, c = r[order], c[order]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    return np.cumsum(row_ptr).astype(np.int32), c.astype(np.int32)
+
+
+class Amg:
+    """Aggregation multigrid hierarchy of a mesh (orc_amg_new) and the
+    V-cycle preconditioned CG for symmetric LDU matrices in the mesh's
+    internal order."""
+
+    def __init__(self, mesh: "Mesh"):
+        self._mesh = mesh
+        self.h = lib().orc_amg_new(mesh.h)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_amg_free(self.h)
+            self.h = None
+
+    def levels(self):
+        n = np.zeros(32, np.int32); ne = np.zeros(32, np.int32)
+        k = lib().orc_amg_levels(self.h, n, ne)
+        return n[:k].copy(), ne[:k].copy()
+
+    def maps(self, l):
+        n, ne = self.levels()
+        agg = np.zeros(max(n[l], 1), np.int32); emap = np.zeros(max(ne[l], 1), np.int32)
+        lib().orc_amg_maps(self.h, l, agg, emap)
+        return agg[:n[l]], emap[:ne[l]]
+
+    def matrix(self, l):
+        """Level-l (diag, off) of the matrix of the last V-cycle or solve."""
+        n, ne = self.levels()
+        d = np.zeros(max(n[l], 1)); o = np.zeros(max(ne[l], 1))
+        lib().orc_amg_matrix(self.h, l, d, o)
+        return d[:n[l]], o[:ne[l]]
+
+    def edges(self, l):
+        n, ne = self.levels()
+        a = np.zeros(max(ne[l], 1), np.int32); b = np.zeros(max(ne[l], 1), np.int32)
+        lib().orc_amg_edges(self.h, l, a, b)
+        return a[:ne[l]], b[:ne[l]]
+
+    def vcycle(self, diag, upper, r):
+        z = np.zeros(len(diag))
+        if lib().orc_amg_vcycle(self.h, _c(diag, np.float64), _c(upper, np.float64),
+                                _c(r, np.float64), z) != 0:
+            raise ValueError("coarsest matrix is not positive definite")
+        return z
+
+    def pcg(self, diag, upper, b, x0, tol=1e-6, reltol=0.0, maxit=10000):
+        x = np.array(x0, dtype=np.float64, copy=True)
+        r0, r1, it = C.c_double(), C.c_double(), C.c_int()
+        st = lib().orc_amg_pcg(self.h, _c(diag, np.float64), _c(upper, np.float64),
+                               _c(b, np.float64), x, tol, reltol, maxit, C.byref(r0),
+                               C.byref(r1), C.byref(it))
+        return x, it.value, r0.value, r1.value, st
+

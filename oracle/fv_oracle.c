@@ -920,13 +920,20 @@ static void correct_velocity(ocase *cs, const pwork *w, double *gradp)
 /* ------------------------------------------------------------------------ */
 /* PISO time step (paper Sec. 3): momentum predictor, then n_corr pressure   */
 /* corrections.  M is assembled once per step; H uses the current u.         */
-/* Per-solve statistics: iters[0..2] momentum components, iters[3..] p;      */
+/* Each corrector solves the pressure equation 1 + n_nonorth times: after a  */
+/* solve, the explicit non-orthogonal part of the right-hand side (and of    */
+/* the face flux) is re-evaluated with the gradient of the new pressure and  */
+/* the equation solved again from that pressure (the non-orthogonal          */
+/* correctors of the textbook method; the paper's Sec. 5 notes their cost on */
+/* the non-orthogonal artery mesh).  The flux is corrected after the last.   */
+/* Per-solve statistics: iters[0..2] momentum components, then one entry per */
+/* pressure solve in order (corrector k, loop j at 3 + k (1 + n_nonorth) + j);*/
 /* res[2k] initial and res[2k+1] final normalised residual of solve k.       */
 /* Returns 0, or the first non-zero solver status.                            */
 /* ------------------------------------------------------------------------ */
 
-int orc_piso_step(ocase *cs, double dt, int n_corr, double p_tol, int p_maxit, double u_tol,
-                  int u_maxit, int ref_orig, double p_ref, int *iters, double *res,
+int orc_piso_step(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol, int p_maxit,
+                  double u_tol, int u_maxit, int ref_orig, double p_ref, int *iters, double *res,
                   double *cont_err)
 {
     const omesh *m = cs->m;
@@ -953,10 +960,14 @@ int orc_piso_step(ocase *cs, double dt, int n_corr, double p_tol, int p_maxit, d
     *cont_err = 0.0;
     for (int k = 0; k < n_corr; ++k) {
         compute_HbyA(cs, mdiag, up, lo, src, &w);
-        assemble_pressure(cs, gradp, ref, p_ref, &w);
-        st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, 0.0, p_maxit,
-                     &res[2 * (3 + k)], &res[2 * (3 + k) + 1], &iters[3 + k]);
-        if (st && !status) status = st;
+        for (int j = 0; j <= n_nonorth; ++j) {
+            const int sk = 3 + k * (n_nonorth + 1) + j;
+            if (j > 0) grad_p(cs, cs->p, gradp);
+            assemble_pressure(cs, gradp, ref, p_ref, &w);
+            st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, 0.0, p_maxit,
+                         &res[2 * sk], &res[2 * sk + 1], &iters[sk]);
+            if (st && !status) status = st;
+        }
         correct_flux(cs, &w);
         double ce = continuity_identity(cs, &w, ref, p_ref);
         if (ce > *cont_err) *cont_err = ce;
@@ -969,7 +980,8 @@ int orc_piso_step(ocase *cs, double dt, int n_corr, double p_tol, int p_maxit, d
 
 /* ------------------------------------------------------------------------ */
 /* SIMPLE iteration (paper Sec. 3).  READINGS: implicit momentum relaxation  */
-/* alpha_u; one pressure solve; the flux is corrected with the unrelaxed    */
+/* alpha_u; 1 + n_nonorth pressure solves (non-orthogonal correctors as in   */
+/* the PISO step); the flux is corrected with the unrelaxed                  */
 /* pressure; then p <- p_old + alpha_p (p_sol - p_old) and                    */
 /* u = HbyA - rAU grad p_relaxed.  Outer convergence measure init_res_max =   */
 /* max of                                                                      */
@@ -979,9 +991,10 @@ int orc_piso_step(ocase *cs, double dt, int n_corr, double p_tol, int p_maxit, d
 /* vanish when a component of the exact solution is zero.                     */
 /* ------------------------------------------------------------------------ */
 
-int orc_simple_iter(ocase *cs, double alpha_u, double alpha_p, double p_tol, double p_reltol,
-                    int p_maxit, double u_tol, double u_reltol, int u_maxit, int ref_orig,
-                    double p_ref, int *iters, double *res, double *cont_err, double *init_res_max)
+int orc_simple_iter(ocase *cs, double alpha_u, double alpha_p, int n_nonorth, double p_tol,
+                    double p_reltol, int p_maxit, double u_tol, double u_reltol, int u_maxit,
+                    int ref_orig, double p_ref, int *iters, double *res, double *cont_err,
+                    double *init_res_max)
 {
     const omesh *m = cs->m;
     int N = m->N, F = m->F;
@@ -1022,9 +1035,15 @@ int orc_simple_iter(ocase *cs, double alpha_u, double alpha_p, double p_tol, dou
         if (rp > irm) irm = rp;
     }
     memcpy(pold, cs->p, sizeof(double) * N);
-    st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, p_reltol, p_maxit,
-                 &res[6], &res[7], &iters[3]);
-    if (st && !status) status = st;
+    for (int j = 0; j <= n_nonorth; ++j) {
+        if (j > 0) {
+            grad_p(cs, cs->p, gradp);
+            assemble_pressure(cs, gradp, ref, p_ref, &w);
+        }
+        st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, p_reltol, p_maxit,
+                     &res[2 * (3 + j)], &res[2 * (3 + j) + 1], &iters[3 + j]);
+        if (st && !status) status = st;
+    }
     correct_flux(cs, &w);
     *cont_err = continuity_identity(cs, &w, ref, p_ref);
     for (int i = 0; i < N; ++i) cs->p[i] = pold[i] + alpha_p * (cs->p[i] - pold[i]);
@@ -1107,4 +1126,418 @@ void orc_case_state(const ocase *cs, double *u, double *p, double *phi)
     memcpy(u, cs->u, sizeof(double) * 3 * m->N);
     memcpy(p, cs->p, sizeof(double) * m->N);
     memcpy(phi, cs->phi, sizeof(double) * (m->F + m->B));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hybrid ELL + J (+ CRS overflow) storage of a structurally symmetric       */
+/* sparsity pattern (paper Sec. 3.1).  Input rows: row_ptr[n+1], col[]       */
+/* ascending within a row, diagonal included.  Row-major N x K arrays as in  */
+/* the paper's example:                                                      */
+/*   ELL: the first K entries of row i; I[i K + k] = column, -1 = empty slot; */
+/*   J[i K + k] = k' with I[j K + k'] = i, j = I[i K + k] (the slot of the    */
+/*   transposed entry in row j); when that entry is in the CRS part at       */
+/*   position p, J = -2 - p; empty slot: J = -1.                               */
+/*   CRS: the entries of a row after its K-th, crs_ptr[n+1], crs_col[], and   */
+/*   crs_tr[p] = the transposed entry's ELL slot (>= 0) or -2 - p'.           */
+/* With crs_col == NULL only crs_ptr is filled.  Returns the number of CRS    */
+/* entries, or -1 if some entry has no transpose (pattern not symmetric).     */
+/* ------------------------------------------------------------------------ */
+
+static int ellj_locate(const int *row_ptr, const int *col, int K, const int *crs_ptr, int j,
+                       int i)
+{
+    /* position of entry (j, i): ELL slot k (>= 0) or -2 - p in the CRS part */
+    int len = row_ptr[j + 1] - row_ptr[j];
+    for (int t = 0; t < len; ++t) {
+        if (col[row_ptr[j] + t] != i) continue;
+        if (t < K) return t;
+        return -2 - (crs_ptr[j] + (t - K));
+    }
+    return -1;
+}
+
+int orc_ellj_build(int n, const int *row_ptr, const int *col, int K, int *I, int *J,
+                   int *crs_ptr, int *crs_col, int *crs_tr)
+{
+    crs_ptr[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        int len = row_ptr[i + 1] - row_ptr[i];
+        crs_ptr[i + 1] = crs_ptr[i] + (len > K ? len - K : 0);
+    }
+    int ncrs = crs_ptr[n];
+    if (crs_col == NULL) return ncrs;
+    for (int i = 0; i < n; ++i) {
+        int len = row_ptr[i + 1] - row_ptr[i];
+        for (int k = 0; k < K; ++k) {
+            if (k < len) {
+                int j = col[row_ptr[i] + k];
+                int loc = ellj_locate(row_ptr, col, K, crs_ptr, j, i);
+                if (loc == -1) return -1;
+                I[(size_t)i * K + k] = j;
+                J[(size_t)i * K + k] = loc;
+            } else {
+                I[(size_t)i * K + k] = -1;
+                J[(size_t)i * K + k] = -1;
+            }
+        }
+        for (int t = K; t < len; ++t) {
+            int j = col[row_ptr[i] + t];
+            int p = crs_ptr[i] + (t - K);
+            int loc = ellj_locate(row_ptr, col, K, crs_ptr, j, i);
+            if (loc == -1) return -1;
+            crs_col[p] = j;
+            crs_tr[p] = loc;
+        }
+    }
+    return ncrs;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Aggregation multigrid preconditioner for the pressure CG (the stronger     */
+/* pressure solver the paper's Sec. 5 and 6 call for; the paper itself runs  */
+/* only Jacobi-CG on the GPU and compares with OpenFOAM's GAMG on the CPU).   */
+/*                                                                            */
+/* Setup, from the mesh alone: level 0 is the cell graph with edge weights    */
+/* |S_f| Delta_f (the face coefficient of the Laplacian without rAU).  A      */
+/* level's aggregates come from two pairwise-matching passes; each pass      */
+/* visits the nodes in index order and pairs an unassigned node with its     */
+/* unassigned neighbour of largest weight, or, when all its neighbours are   */
+/* taken, adds it to the aggregate of its strongest neighbour (a node with   */
+/* no neighbour stays alone).  Weights within a relative 1e-9 count as equal */
+/* and the lower index wins.  The coarse graph joins two aggregates that     */
+/* share a fine edge, with the summed weight; its edges are ordered by       */
+/* (lower, higher) aggregate.  Coarsening stops at <= 32 nodes or when a     */
+/* level shrinks by less than 10 %; the last level is solved directly.        */
+/*                                                                            */
+/* Per matrix (symmetric LDU: diag, upper): Galerkin coarse matrices with     */
+/* piecewise-constant prolongation, A_c = P^T A P: a coarse diagonal sums the */
+/* members' diagonals (ascending) and twice the coefficients of the faces    */
+/* inside the aggregate (ascending); a coarse face sums its fine faces'       */
+/* coefficients (ascending).  The coarsest matrix is factored by Cholesky.   */
+/*                                                                            */
+/* V-cycle z = M r: per level, from x = 0, nu = 2 weighted-Jacobi sweeps      */
+/* x += omega (b - A x) / diag (omega = 2/3), the residual restricted by     */
+/* summing over each aggregate, the coarse problem solved by the same cycle, */
+/* the correction added with the over-correction factor alpha = 1.8 (the     */
+/* plain piecewise-constant correction is too small in energy; alpha < 2     */
+/* keeps the cycle symmetric positive definite), and nu = 2 sweeps again.    */
+/* ------------------------------------------------------------------------ */
+
+#define AMG_MAXLEV 24
+#define AMG_OMEGA (2.0 / 3.0)
+#define AMG_ALPHA 1.8
+#define AMG_NU 2
+#define AMG_NMIN 32
+#define AMG_TIE 1e-9
+
+typedef struct {
+    int nlev;
+    int n[AMG_MAXLEV], ne[AMG_MAXLEV];
+    int *ea[AMG_MAXLEV], *eb[AMG_MAXLEV];    /* edges of level l, ea < eb */
+    int *agg[AMG_MAXLEV];                    /* level l node -> level l+1 node */
+    int *emap[AMG_MAXLEV];                   /* level l edge -> level l+1 edge or -1 */
+    double *d[AMG_MAXLEV], *o[AMG_MAXLEV];   /* current matrices */
+    double *chol;                            /* coarsest Cholesky factor, row-major */
+} oamg;
+
+static int amg_better(double wc, int jc, double wb, int jb)
+{
+    if (jb < 0) return 1;
+    if (wc > wb * (1.0 + AMG_TIE)) return 1;
+    if (wc >= wb * (1.0 - AMG_TIE) && jc < jb) return 1;
+    return 0;
+}
+
+/* one pairwise-matching pass over a graph; returns the number of aggregates */
+static int amg_pass(int n, int ne, const int *ea, const int *eb, const double *ew, int *assign)
+{
+    int *deg = xcalloc(n + 1, sizeof(int));
+    for (int e = 0; e < ne; ++e) { deg[ea[e] + 1]++; deg[eb[e] + 1]++; }
+    for (int i = 0; i < n; ++i) deg[i + 1] += deg[i];
+    int *fill = xcalloc(n, sizeof(int)), *adj = xcalloc(2 * (size_t)ne + 1, sizeof(int));
+    double *aw = xcalloc(2 * (size_t)ne + 1, sizeof(double));
+    for (int e = 0; e < ne; ++e) {
+        int a = ea[e], b = eb[e];
+        adj[deg[a] + fill[a]] = b; aw[deg[a] + fill[a]++] = ew[e];
+        adj[deg[b] + fill[b]] = a; aw[deg[b] + fill[b]++] = ew[e];
+    }
+    for (int i = 0; i < n; ++i) assign[i] = -1;
+    int na = 0;
+    for (int i = 0; i < n; ++i) {
+        if (assign[i] >= 0) continue;
+        int bj = -1; double bw = 0.0;
+        for (int t = deg[i]; t < deg[i + 1]; ++t)
+            if (assign[adj[t]] < 0 && amg_better(aw[t], adj[t], bw, bj)) { bj = adj[t]; bw = aw[t]; }
+        if (bj >= 0) { assign[i] = assign[bj] = na++; continue; }
+        bj = -1; bw = 0.0;
+        for (int t = deg[i]; t < deg[i + 1]; ++t)
+            if (amg_better(aw[t], adj[t], bw, bj)) { bj = adj[t]; bw = aw[t]; }
+        assign[i] = bj >= 0 ? assign[bj] : na++;
+    }
+    free(deg); free(fill); free(adj); free(aw);
+    return na;
+}
+
+typedef struct { int lo, hi, e; } amg_key;
+
+static int amg_key_cmp(const void *x, const void *y)
+{
+    const amg_key *a = x, *b = y;
+    if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;
+    if (a->hi != b->hi) return a->hi < b->hi ? -1 : 1;
+    return a->e < b->e ? -1 : (a->e > b->e);
+}
+
+/* coarse graph of an assignment: edges, summed weights, fine edge -> coarse */
+static int amg_coarse_graph(int ne, const int *ea, const int *eb, const double *ew,
+                            const int *assign, int **cea, int **ceb, double **cew, int *emap)
+{
+    amg_key *k = xcalloc(ne + 1, sizeof(amg_key));
+    int m = 0;
+    for (int e = 0; e < ne; ++e) {
+        int a = assign[ea[e]], b = assign[eb[e]];
+        if (a == b) { emap[e] = -1; continue; }
+        k[m].lo = a < b ? a : b; k[m].hi = a < b ? b : a; k[m].e = e; ++m;
+    }
+    qsort(k, m, sizeof(amg_key), amg_key_cmp);
+    int nc = 0;
+    for (int t = 0; t < m; ++t)
+        if (t == 0 || k[t].lo != k[t - 1].lo || k[t].hi != k[t - 1].hi) ++nc;
+    *cea = xcalloc(nc + 1, sizeof(int)); *ceb = xcalloc(nc + 1, sizeof(int));
+    *cew = xcalloc(nc + 1, sizeof(double));
+    int c = -1;
+    for (int t = 0; t < m; ++t) {
+        if (t == 0 || k[t].lo != k[t - 1].lo || k[t].hi != k[t - 1].hi) {
+            ++c; (*cea)[c] = k[t].lo; (*ceb)[c] = k[t].hi; (*cew)[c] = 0.0;
+        }
+        emap[k[t].e] = c;
+    }
+    /* weights summed in ascending fine-edge order */
+    for (int e = 0; e < ne; ++e) if (emap[e] >= 0) (*cew)[emap[e]] += ew[e];
+    free(k);
+    return nc;
+}
+
+oamg *orc_amg_new(const omesh *m)
+{
+    oamg *h = xcalloc(1, sizeof(oamg));
+    int n = m->N, ne = m->F;
+    int *ea = xcalloc(ne + 1, sizeof(int)), *eb = xcalloc(ne + 1, sizeof(int));
+    double *ew = xcalloc(ne + 1, sizeof(double));
+    for (int f = 0; f < ne; ++f) {
+        ea[f] = m->own[f]; eb[f] = m->nei[f];
+        ew[f] = m->magSf[f] * m->delta[f];
+    }
+    int l = 0;
+    for (;;) {
+        h->n[l] = n; h->ne[l] = ne; h->ea[l] = ea; h->eb[l] = eb;
+        h->d[l] = xcalloc(n + 1, sizeof(double)); h->o[l] = xcalloc(ne + 1, sizeof(double));
+        if (n <= AMG_NMIN || l + 1 >= AMG_MAXLEV) { free(ew); break; }
+        int *a1 = xcalloc(n + 1, sizeof(int)), *m1 = xcalloc(ne + 1, sizeof(int));
+        int n1 = amg_pass(n, ne, ea, eb, ew, a1);
+        int *ea1, *eb1; double *ew1;
+        int ne1 = amg_coarse_graph(ne, ea, eb, ew, a1, &ea1, &eb1, &ew1, m1);
+        int *a2 = xcalloc(n1 + 1, sizeof(int)), *m2 = xcalloc(ne1 + 1, sizeof(int));
+        int n2 = amg_pass(n1, ne1, ea1, eb1, ew1, a2);
+        int *ea2, *eb2; double *ew2;
+        int ne2 = amg_coarse_graph(ne1, ea1, eb1, ew1, a2, &ea2, &eb2, &ew2, m2);
+        free(ea1); free(eb1); free(ew1);
+        if ((double)n2 > 0.9 * n) {
+            free(a1); free(m1); free(a2); free(m2); free(ea2); free(eb2); free(ew2); free(ew);
+            break;
+        }
+        h->agg[l] = xcalloc(n + 1, sizeof(int));
+        h->emap[l] = xcalloc(ne + 1, sizeof(int));
+        for (int i = 0; i < n; ++i) h->agg[l][i] = a2[a1[i]];
+        for (int e = 0; e < ne; ++e) h->emap[l][e] = m1[e] < 0 ? -1 : m2[m1[e]];
+        free(a1); free(m1); free(a2); free(m2); free(ew);
+        n = n2; ne = ne2; ea = ea2; eb = eb2; ew = ew2;
+        ++l;
+    }
+    h->nlev = l + 1;
+    int nc = h->n[l];
+    h->chol = xcalloc((size_t)nc * nc + 1, sizeof(double));
+    return h;
+}
+
+void orc_amg_free(oamg *h)
+{
+    if (!h) return;
+    for (int l = 0; l < h->nlev; ++l) {
+        free(h->ea[l]); free(h->eb[l]); free(h->agg[l]); free(h->emap[l]);
+        free(h->d[l]); free(h->o[l]);
+    }
+    free(h->chol);
+    free(h);
+}
+
+int orc_amg_levels(const oamg *h, int *n, int *ne)
+{
+    for (int l = 0; l < h->nlev; ++l) { n[l] = h->n[l]; ne[l] = h->ne[l]; }
+    return h->nlev;
+}
+
+/* aggregate map and edge map of level l (l < nlev - 1) */
+void orc_amg_maps(const oamg *h, int l, int *agg, int *emap)
+{
+    memcpy(agg, h->agg[l], sizeof(int) * h->n[l]);
+    memcpy(emap, h->emap[l], sizeof(int) * h->ne[l]);
+}
+
+/* Galerkin coarse matrices and the coarsest factor; returns -1 if the
+ * coarsest matrix is not positive definite. */
+static int amg_set_matrix(oamg *h, const double *diag, const double *upper)
+{
+    memcpy(h->d[0], diag, sizeof(double) * h->n[0]);
+    memcpy(h->o[0], upper, sizeof(double) * h->ne[0]);
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+        double *cd = h->d[l + 1], *co = h->o[l + 1];
+        for (int I = 0; I < h->n[l + 1]; ++I) cd[I] = 0.0;
+        for (int E = 0; E < h->ne[l + 1]; ++E) co[E] = 0.0;
+        for (int i = 0; i < h->n[l]; ++i) cd[h->agg[l][i]] += h->d[l][i];
+        for (int e = 0; e < h->ne[l]; ++e)
+            if (h->emap[l][e] < 0) cd[h->agg[l][h->ea[l][e]]] += 2.0 * h->o[l][e];
+        for (int e = 0; e < h->ne[l]; ++e)
+            if (h->emap[l][e] >= 0) co[h->emap[l][e]] += h->o[l][e];
+    }
+    int L = h->nlev - 1, n = h->n[L];
+    double *c = h->chol;
+    for (size_t t = 0; t < (size_t)n * n; ++t) c[t] = 0.0;
+    for (int i = 0; i < n; ++i) c[(size_t)i * n + i] = h->d[L][i];
+    for (int e = 0; e < h->ne[L]; ++e) {
+        c[(size_t)h->ea[L][e] * n + h->eb[L][e]] = h->o[L][e];
+        c[(size_t)h->eb[L][e] * n + h->ea[L][e]] = h->o[L][e];
+    }
+    /* Cholesky A = L L^T, L stored in the lower triangle */
+    for (int j = 0; j < n; ++j) {
+        double s = c[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= c[(size_t)j * n + k] * c[(size_t)j * n + k];
+        if (!(s > 0.0)) return -1;
+        double ljj = sqrt(s);
+        c[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = c[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= c[(size_t)i * n + k] * c[(size_t)j * n + k];
+            c[(size_t)i * n + j] = t / ljj;
+        }
+    }
+    return 0;
+}
+
+static void amg_sweep(const oamg *h, int l, const double *b, double *x, double *t)
+{
+    int n = h->n[l];
+    ldu_matvec(n, h->ne[l], h->ea[l], h->eb[l], h->d[l], h->o[l], h->o[l], x, t);
+    for (int i = 0; i < n; ++i) x[i] += AMG_OMEGA * (b[i] - t[i]) / h->d[l][i];
+}
+
+static void amg_vcycle(const oamg *h, int l, const double *b, double *x)
+{
+    int n = h->n[l];
+    if (l == h->nlev - 1) {
+        const double *c = h->chol;
+        for (int i = 0; i < n; ++i) {            /* L y = b */
+            double s = b[i];
+            for (int k = 0; k < i; ++k) s -= c[(size_t)i * n + k] * x[k];
+            x[i] = s / c[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {       /* L^T x = y */
+            double s = x[i];
+            for (int k = i + 1; k < n; ++k) s -= c[(size_t)k * n + i] * x[k];
+            x[i] = s / c[(size_t)i * n + i];
+        }
+        return;
+    }
+    double *t = xcalloc(n + 1, sizeof(double));
+    for (int i = 0; i < n; ++i) x[i] = AMG_OMEGA * b[i] / h->d[l][i];
+    for (int s = 1; s < AMG_NU; ++s) amg_sweep(h, l, b, x, t);
+    ldu_matvec(n, h->ne[l], h->ea[l], h->eb[l], h->d[l], h->o[l], h->o[l], x, t);
+    int nc = h->n[l + 1];
+    double *bc = xcalloc(nc + 1, sizeof(double)), *xc = xcalloc(nc + 1, sizeof(double));
+    for (int i = 0; i < n; ++i) bc[h->agg[l][i]] += b[i] - t[i];
+    amg_vcycle(h, l + 1, bc, xc);
+    for (int i = 0; i < n; ++i) x[i] += AMG_ALPHA * xc[h->agg[l][i]];
+    for (int s = 0; s < AMG_NU; ++s) amg_sweep(h, l, b, x, t);
+    free(t); free(bc); free(xc);
+}
+
+/* one V-cycle z = M r for the matrix (diag, upper); returns -1 if the
+ * coarsest matrix is not positive definite */
+int orc_amg_vcycle(oamg *h, const double *diag, const double *upper, const double *r, double *z)
+{
+    if (amg_set_matrix(h, diag, upper)) return -1;
+    amg_vcycle(h, 0, r, z);
+    return 0;
+}
+
+/* CG preconditioned by the V-cycle; the stopping rule, warm start and
+ * statistics are those of orc_pcg. */
+int orc_amg_pcg(oamg *h, const double *diag, const double *upper, const double *b, double *x,
+                double tol, double reltol, int maxit, double *res0_out, double *res_out,
+                int *iters_out)
+{
+    int N = h->n[0], F = h->ne[0];
+    const int *own = h->ea[0], *nei = h->eb[0];
+    double *r = xcalloc(N, sizeof(double)), *z = xcalloc(N, sizeof(double));
+    double *p = xcalloc(N, sizeof(double)), *q = xcalloc(N, sizeof(double));
+    int status = 0, it = 0;
+    double nb = norm2_n(N, b);
+    if (nb == 0.0) {
+        for (int i = 0; i < N; ++i) x[i] = 0.0;
+        *res0_out = 0.0; *res_out = 0.0; *iters_out = 0;
+        free(r); free(z); free(p); free(q);
+        return 0;
+    }
+    if (amg_set_matrix(h, diag, upper)) {
+        *res0_out = *res_out = 0.0; *iters_out = 0;
+        free(r); free(z); free(p); free(q);
+        return -2;
+    }
+    ldu_matvec(N, F, own, nei, diag, upper, upper, x, q);
+    for (int i = 0; i < N; ++i) r[i] = b[i] - q[i];
+    double nr = norm2_n(N, r);
+    double thresh = tol * nb;
+    if (reltol * nr > thresh) thresh = reltol * nr;
+    *res0_out = nr / nb;
+    if (nr <= thresh) goto done;
+    amg_vcycle(h, 0, r, z);
+    for (int i = 0; i < N; ++i) p[i] = z[i];
+    double rho = dot_n(N, r, z);
+    for (it = 1; it <= maxit; ++it) {
+        ldu_matvec(N, F, own, nei, diag, upper, upper, p, q);
+        double pq = dot_n(N, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = -2; break; }
+        double alpha = rho / pq;
+        for (int i = 0; i < N; ++i) x[i] += alpha * p[i];
+        for (int i = 0; i < N; ++i) r[i] -= alpha * q[i];
+        nr = norm2_n(N, r);
+        if (!isfinite(nr)) { status = -2; break; }
+        if (nr <= thresh) break;
+        if (it == maxit) { status = -1; break; }
+        amg_vcycle(h, 0, r, z);
+        double rho_new = dot_n(N, r, z);
+        double beta = rho_new / rho;
+        rho = rho_new;
+        for (int i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (it > maxit) status = -1;
+done:
+    *res_out = nr / nb;
+    *iters_out = it > maxit ? maxit : it;
+    free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* level-l matrices set by the last V-cycle or solve (tests) */
+void orc_amg_matrix(const oamg *h, int l, double *d, double *o)
+{
+    memcpy(d, h->d[l], sizeof(double) * h->n[l]);
+    memcpy(o, h->o[l], sizeof(double) * h->ne[l]);
+}
+
+/* edges of level l (tests) */
+void orc_amg_edges(const oamg *h, int l, int *ea, int *eb)
+{
+    memcpy(ea, h->ea[l], sizeof(int) * h->ne[l]);
+    memcpy(eb, h->eb[l], sizeof(int) * h->ne[l]);
 }

@@ -22,7 +22,7 @@ from . import _capi
 from ._capi import (FV_PREC_FP64, FV_PREC_MIXED, FV_E_NOT_CONVERGED, FV_OK, FvError,  # noqa
                     check, load)
 
-__all__ = ["Mesh", "Case", "Batch", "mesh_plan", "load", "FvError", "FV_PREC_FP64",
+__all__ = ["Mesh", "Case", "Batch", "Ellj", "mesh_plan", "ellj_build_host", "load", "FvError", "FV_PREC_FP64",
            "FV_PREC_MIXED"]
 
 
@@ -196,6 +196,73 @@ class Mesh:
         return y
 
 
+def ellj_build_host(row_ptr, col, K: int) -> dict:
+    """Host-only hybrid ELL + J + CRS arrays of a structurally symmetric
+    pattern (``fv_ellj_build_host``): I, J as n x K arrays, crs_ptr,
+    crs_col, crs_tr.  Touches no GPU."""
+    L = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(row_ptr) - 1
+    crs_ptr = np.zeros(n + 1, np.int32)
+    ncrs = C.c_int32()
+    check(L.fv_ellj_build_host(n, row_ptr.ctypes.data, col.ctypes.data, K, None, None,
+                               crs_ptr.ctypes.data, None, None, C.byref(ncrs)), "fv_ellj_build_host")
+    I = np.zeros((n, K), np.int32)
+    J = np.zeros((n, K), np.int32)
+    crs_col = np.zeros(max(ncrs.value, 1), np.int32)
+    crs_tr = np.zeros(max(ncrs.value, 1), np.int32)
+    check(L.fv_ellj_build_host(n, row_ptr.ctypes.data, col.ctypes.data, K, I.ctypes.data,
+                               J.ctypes.data, crs_ptr.ctypes.data, crs_col.ctypes.data,
+                               crs_tr.ctypes.data, C.byref(ncrs)), "fv_ellj_build_host")
+    return dict(I=I, J=J, crs_ptr=crs_ptr, crs_col=crs_col[:ncrs.value], crs_tr=crs_tr[:ncrs.value])
+
+
+class Ellj:
+    """The paper's hybrid ELL + J (+ CRS) storage of a mesh's LDU pattern
+    (``fv_ellj_create``), with assembly from LDU coefficients and the row
+    and column products."""
+
+    def __init__(self, mesh: Mesh, K: int = 0):
+        self.mesh, self.L = mesh, mesh.L
+        h = C.c_void_p()
+        check(self.L.fv_ellj_create(mesh.h, K, C.byref(h)), "fv_ellj_create")
+        self.h = h
+        k, n = C.c_int32(), C.c_int32()
+        check(self.L.fv_ellj_info(self.h, C.byref(k), C.byref(n)), "fv_ellj_info")
+        self.K, self.n_crs = k.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fv_ellj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def from_ldu(self, diag, upper, lower):
+        """(V [K*N], C [n_crs]) device tensors holding the LDU matrix."""
+        V = self.mesh._new(self.K * self.mesh.N)
+        Cv = self.mesh._new(max(self.n_crs, 1))
+        self.mesh._enter(diag, upper, lower, V, Cv)
+        check(self.L.fv_ellj_from_ldu(self.h, diag.data_ptr(), _ptr(upper), _ptr(lower),
+                                      V.data_ptr(), Cv.data_ptr()), "fv_ellj_from_ldu")
+        self.mesh._leave()
+        return V, Cv
+
+    def spmv(self, V, Cv, x, mode: int = 0, y=None):
+        """mode 0: A x; 1: A^T x through I and J; 2: A^T x through Q."""
+        y = self.mesh._new(self.mesh.N) if y is None else y
+        self.mesh._enter(V, Cv, x, y)
+        check(self.L.fv_ellj_spmv(self.h, V.data_ptr(), Cv.data_ptr(), x.data_ptr(), y.data_ptr(),
+                                  mode), "fv_ellj_spmv")
+        self.mesh._leave()
+        return y
+
+
 class Case:
     """A flow case (``fv_case_create``): fields u, p, phi and boundary values."""
 
@@ -283,12 +350,14 @@ class Case:
 
     @staticmethod
     def piso_params(dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10, u_maxit=1000,
-                    p_ref_cell=-1, p_ref=0.0):
-        return _capi.fv_piso_params(dt, n_corr, p_maxit, p_tol, u_tol, u_maxit, p_ref_cell, p_ref)
+                    p_ref_cell=-1, p_ref=0.0, n_nonorth=0):
+        return _capi.fv_piso_params(dt, n_corr, p_maxit, p_tol, u_tol, u_maxit, p_ref_cell, p_ref,
+                                    n_nonorth, 0)
 
     def piso_step(self, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10, u_maxit=1000,
-                  p_ref_cell=-1, p_ref=0.0, stats=True):
-        prm = self.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, p_ref_cell, p_ref)
+                  p_ref_cell=-1, p_ref=0.0, stats=True, n_nonorth=0):
+        prm = self.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, p_ref_cell, p_ref,
+                               n_nonorth)
         self.mesh._enter()
         if not stats:
             check(self.L.fv_piso_step(self.h, C.byref(prm), None), "fv_piso_step")
@@ -299,8 +368,9 @@ class Case:
         return _step_dict(s)
 
     def run_graph(self, n_steps, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10,
-                  u_maxit=1000, p_ref_cell=-1, p_ref=0.0, stats=True):
-        prm = self.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, p_ref_cell, p_ref)
+                  u_maxit=1000, p_ref_cell=-1, p_ref=0.0, stats=True, n_nonorth=0):
+        prm = self.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, p_ref_cell, p_ref,
+                               n_nonorth)
         self.mesh._enter()
         s = _capi.fv_step_stats() if stats else None
         rc = self.L.fv_piso_run_graph(self.h, C.byref(prm), n_steps, C.byref(s) if stats else None)
@@ -308,9 +378,10 @@ class Case:
         return _step_dict(s) if stats else None
 
     def simple_iter(self, alpha_u=0.7, alpha_p=0.3, p_tol=1e-10, p_reltol=0.01, p_maxit=10000,
-                    u_tol=1e-10, u_reltol=0.1, u_maxit=1000, p_ref_cell=-1, p_ref=0.0, stats=True):
+                    u_tol=1e-10, u_reltol=0.1, u_maxit=1000, p_ref_cell=-1, p_ref=0.0, stats=True,
+                    n_nonorth=0):
         prm = _capi.fv_simple_params(alpha_u, alpha_p, p_tol, p_reltol, u_tol, u_reltol, p_maxit,
-                                     u_maxit, p_ref_cell, 0, p_ref)
+                                     u_maxit, p_ref_cell, n_nonorth, p_ref)
         self.mesh._enter()
         if not stats:
             check(self.L.fv_simple_iter(self.h, C.byref(prm), None), "fv_simple_iter")
@@ -360,8 +431,8 @@ class Batch:
         return [_step_dict(arr[k]) for k in range(self.n)]
 
     def piso_step(self, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10, u_maxit=1000,
-                  stats=True):
-        prm = Case.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, -1, 0.0)
+                  stats=True, n_nonorth=0):
+        prm = Case.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, -1, 0.0, n_nonorth)
         arr = (_capi.fv_step_stats * self.n)() if stats else None
         self._torch_wait()
         rc = self.L.fv_batch_piso_step(self.h, C.byref(prm), arr)
@@ -369,8 +440,8 @@ class Batch:
         return self._stats(arr) if stats else None
 
     def run_graph(self, n_steps, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10,
-                  u_maxit=1000, stats=True):
-        prm = Case.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, -1, 0.0)
+                  u_maxit=1000, stats=True, n_nonorth=0):
+        prm = Case.piso_params(dt, n_corr, p_tol, p_maxit, u_tol, u_maxit, -1, 0.0, n_nonorth)
         arr = (_capi.fv_step_stats * self.n)() if stats else None
         self._torch_wait()
         rc = self.L.fv_batch_run_graph(self.h, C.byref(prm), n_steps, arr)

@@ -29,7 +29,8 @@ EXPORTS = [
     "fv_profile_enable", "fv_profile_read", "fv_case_last_stats", "fv_pcg_solve_noalloc",
     "fv_pcg_solve_mixed", "fv_batch_create", "fv_batch_destroy", "fv_batch_piso_step",
     "fv_batch_run_graph", "fv_batch_get_fields", "fv_batch_schedule_info", "fv_batch_set_schedule",
-    "fv_batch_autotune",
+    "fv_batch_autotune", "fv_ellj_build_host", "fv_ellj_create", "fv_ellj_destroy", "fv_ellj_info",
+    "fv_ellj_from_ldu", "fv_ellj_spmv",
 ]
 PROF_STAGES = ["momentum", "bicgstab", "hbya", "pressure", "pcg", "correct", "other"]
 
@@ -60,14 +61,15 @@ class fv_step_stats(C.Structure):
 class fv_piso_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_corr", C.c_int32), ("p_maxit", C.c_int32),
                 ("p_tol", C.c_double), ("u_tol", C.c_double), ("u_maxit", C.c_int32),
-                ("p_ref_cell", C.c_int32), ("p_ref_value", C.c_double)]
+                ("p_ref_cell", C.c_int32), ("p_ref_value", C.c_double),
+                ("n_nonorth", C.c_int32), ("pad_", C.c_int32)]
 
 
 class fv_simple_params(C.Structure):
     _fields_ = [("alpha_u", C.c_double), ("alpha_p", C.c_double), ("p_tol", C.c_double),
                 ("p_reltol", C.c_double), ("u_tol", C.c_double), ("u_reltol", C.c_double),
                 ("p_maxit", C.c_int32), ("u_maxit", C.c_int32), ("p_ref_cell", C.c_int32),
-                ("pad_", C.c_int32), ("p_ref_value", C.c_double)]
+                ("n_nonorth", C.c_int32), ("p_ref_value", C.c_double)]
 
 
 class fv_pcg_params(C.Structure):
@@ -123,6 +125,12 @@ def load(path: str = LIB_PATH):
         "fv_bicgstab_solve": [vp, vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_gauss_grad": [vp, vp, vp, vp],
         "fv_ldu_matvec": [vp, vp, vp, vp, vp, vp],
+        "fv_ellj_build_host": [i32, vp, vp, i32, vp, vp, vp, vp, vp, vp],
+        "fv_ellj_create": [vp, i32, P(vp)],
+        "fv_ellj_destroy": [vp],
+        "fv_ellj_info": [vp, vp, vp],
+        "fv_ellj_from_ldu": [vp, vp, vp, vp, vp, vp],
+        "fv_ellj_spmv": [vp, vp, vp, vp, vp, i32],
         "fv_set_barrier_spin_limit": [C.c_int64],
         "fv_case_memory": [vp, P(C.c_int64)],
         "fv_profile_enable": [i32],

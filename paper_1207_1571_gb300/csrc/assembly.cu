@@ -364,6 +364,47 @@ __global__ void __launch_bounds__(kAsmBlock) k_correct(MeshView m, CorrArgs a)
     a.u[2 * N + i] = a.HbyA[2 * N + i] - r * g2;
 }
 
+// Gauss gradient of the pressure with its boundary values (fixed on
+// outlets, zero-gradient elsewhere): the same sums as in k_correct, for the
+// non-orthogonal correctors that re-evaluate the explicit term.
+__global__ void __launch_bounds__(kAsmBlock) k_grad_p(MeshView m, const double *__restrict__ p,
+                                                      const double *__restrict__ pb,
+                                                      double *__restrict__ gradp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const size_t N = m.N;
+    const int s = i >> 5;
+    const int e0 = m.slice_ptr[s] + (i & 31), K = (m.slice_ptr[s + 1] - m.slice_ptr[s]) >> 5;
+    const double pP = p[i];
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const int e = e0 + 32 * k;
+        const int f = m.sface[e];
+        if (f < 0) continue;
+        const int c = m.col[e];
+        const bool own = i < c;
+        const int lo = own ? i : c, hi = own ? c : i;
+        const double w = m.w[f], sg = own ? 1.0 : -1.0;
+        const double pf = w * p[lo] + (1.0 - w) * p[hi];
+        g0 += sg * m.Sf[f] * pf;
+        g1 += sg * m.Sf[m.M + f] * pf;
+        g2 += sg * m.Sf[2 * m.M + f] * pf;
+    }
+    for (int j = m.bptr[i]; j < m.bptr[i + 1]; ++j) {
+        const int b = m.bface[j];
+        const int fb = m.F + b;
+        const double pbv = m.btype[b] == FV_PATCH_OUTLET ? pb[b] : pP;
+        g0 += m.Sf[fb] * pbv;
+        g1 += m.Sf[m.M + fb] * pbv;
+        g2 += m.Sf[2 * m.M + fb] * pbv;
+    }
+    const double vi = m.Vinv[i];
+    gradp[i] = g0 * vi;
+    gradp[N + i] = g1 * vi;
+    gradp[2 * N + i] = g2 * vi;
+}
+
 // SIMPLE, first half: flux from the solved pressure p, relaxed pressure
 // prelax = pold + alpha_p (p - pold) (cell-local).
 __global__ void __launch_bounds__(kAsmBlock) k_flux_relax(MeshView m, CorrArgs a)
@@ -643,6 +684,23 @@ __global__ void k_permute_faces(int M, const int32_t *__restrict__ no, const int
     else dst[f] = sg * src[g];
 }
 
+// Uniform boundary value on boundary faces [start, start + n): u (if
+// set_u) and p.  Values travel as kernel arguments, so the fill is
+// stream-ordered, needs no host staging and can be captured in a graph.
+__global__ void k_patch_fill(int B, int start, int n, int set_u, double u0, double u1, double u2,
+                             double p, double *__restrict__ ub, double *__restrict__ pb)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const size_t b = (size_t)start + j;
+    if (set_u) {
+        ub[b] = u0;
+        ub[(size_t)B + b] = u1;
+        ub[2 * (size_t)B + b] = u2;
+    }
+    pb[b] = p;
+}
+
 // ------------------------------------------------------------ launches --
 
 #define LAUNCH_CHECK() FV_CUDA(cudaGetLastError())
@@ -680,6 +738,14 @@ fv_status launch_pressure(const fv_case *c, const StepArgs &s)
     PresArgs a{c->HbyA, c->rAU, c->ub, c->pb, c->gradp, s.ref_cell, s.p_ref, c->pin,
                c->Pd, c->Po, c->pbv, c->phis, c->af, c->nof};
     k_pressure<<<blocks_for(m->N), kAsmBlock, 0, m->stream>>>(view(m), a);
+    LAUNCH_CHECK();
+    return FV_OK;
+}
+
+fv_status launch_grad_p(const fv_case *c)
+{
+    const fv_mesh *m = c->mesh;
+    k_grad_p<<<blocks_for(m->N), kAsmBlock, 0, m->stream>>>(view(m), c->p, c->pb, c->gradp);
     LAUNCH_CHECK();
     return FV_OK;
 }
@@ -758,6 +824,16 @@ fv_status launch_permute_cells(const fv_mesh *m, int ncomp, const double *src, d
 {
     k_permute_cells<<<blocks_for(m->N), kAsmBlock, 0, m->stream>>>(m->N, ncomp, m->cell_new_of_old,
                                                                    src, dst, to_internal);
+    LAUNCH_CHECK();
+    return FV_OK;
+}
+
+fv_status launch_patch_fill(const fv_case *c, int start, int n, const double *u, double p)
+{
+    const fv_mesh *m = c->mesh;
+    if (n <= 0) return FV_OK;
+    k_patch_fill<<<blocks_for(n), kAsmBlock, 0, m->stream>>>(
+        m->B, start, n, u != nullptr, u ? u[0] : 0.0, u ? u[1] : 0.0, u ? u[2] : 0.0, p, c->ub, c->pb);
     LAUNCH_CHECK();
     return FV_OK;
 }

@@ -889,10 +889,14 @@ fv_status batch_enqueue(fv_batch *bt, const fv_piso_params *prm)
     if (m->nonorth) BSTAGE(FV_PROF_MOMENTUM, 1, launch_grad_u(c));
     BSTAGE(FV_PROF_MOMENTUM, 1, launch_momentum(c, sa));
     BSTAGE(FV_PROF_BICGSTAB, 1, batch_bicgstab(bt, prm));
+    const int nl = 1 + prm->n_nonorth;
     for (int k = 0; k < prm->n_corr; ++k) {
         BSTAGE(FV_PROF_HBYA, 1, launch_hbya(c));
-        BSTAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
-        BSTAGE(FV_PROF_PCG, 1, batch_pcg(bt, prm, k));
+        for (int j = 0; j < nl; ++j) {
+            if (j > 0) BSTAGE(FV_PROF_PRESSURE, 1, launch_grad_p(c));
+            BSTAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
+            BSTAGE(FV_PROF_PCG, 1, batch_pcg(bt, prm, k * nl + j));
+        }
         BSTAGE(FV_PROF_CORRECT, 1, launch_correct_piso(c));
     }
 #undef BSTAGE
@@ -944,6 +948,8 @@ fv_status check_prm(const fv_piso_params *prm)
     FV_CHECK(prm != nullptr, FV_E_INVALID, "params are NULL");
     FV_CHECK(prm->dt > 0.0, FV_E_INVALID, "dt must be positive");
     FV_CHECK(prm->n_corr >= 1 && prm->n_corr <= FV_MAX_CORR, FV_E_INVALID, "bad n_corr");
+    FV_CHECK(prm->n_nonorth >= 0 && prm->n_corr * (1 + prm->n_nonorth) <= FV_MAX_CORR,
+             FV_E_INVALID, "n_corr * (1 + n_nonorth) must be at most %d", FV_MAX_CORR);
     FV_CHECK(prm->p_maxit >= 0 && prm->u_maxit >= 0, FV_E_INVALID, "negative iteration limit");
     return FV_OK;
 }
@@ -1134,7 +1140,7 @@ extern "C" fv_status fv_batch_piso_step(fv_batch *bt, const fv_piso_params *prm,
     if (st != FV_OK) return st;
     if ((st = batch_enqueue(bt, prm)) != FV_OK) return st;
     if (!per_case) return FV_OK;
-    return batch_stats(bt, prm->n_corr, per_case);
+    return batch_stats(bt, prm->n_corr * (1 + prm->n_nonorth), per_case);
 }
 
 extern "C" fv_status fv_batch_run_graph(fv_batch *bt, const fv_piso_params *prm, int32_t n_steps,
@@ -1163,7 +1169,7 @@ extern "C" fv_status fv_batch_run_graph(fv_batch *bt, const fv_piso_params *prm,
     }
     for (int k = 0; k < n_steps; ++k) FV_CUDA(cudaGraphLaunch(bt->graph, s));
     if (!per_case) return FV_OK;
-    return batch_stats(bt, prm->n_corr, per_case);
+    return batch_stats(bt, prm->n_corr * (1 + prm->n_nonorth), per_case);
 }
 
 extern "C" fv_status fv_batch_get_fields(const fv_batch *bt, int32_t c, double *u, double *p,

@@ -4,8 +4,9 @@
 // A PISO step is a fixed sequence of launches on the mesh's stream:
 //   [grad u (non-orthogonal meshes)] -> momentum assembly + grad p ->
 //   BiCGStab (three components, one cooperative launch) ->
-//   n_corr x { H/A and rAU -> pressure assembly -> CG (one cooperative
-//   launch) -> flux + velocity correction }.
+//   n_corr x { H/A and rAU -> (1 + n_nonorth) x { [grad p] -> pressure
+//   assembly -> CG (one cooperative launch) } -> flux + velocity
+//   correction }.
 // Nothing leaves the device inside a step; statistics are copied back only
 // when the caller asks for them.  Because the sequence is fixed, it can be
 // captured once into a CUDA graph and replayed.
@@ -126,11 +127,16 @@ fv_status piso_enqueue(fv_case *c, const fv_piso_params *prm, int ref)
     BicgProblem bp{c->Md, c->Mo, nullptr, c->src, c->gradp, c->u, 3, prm->u_tol, 0.0,
                    prm->u_maxit, c->dstats};
     STAGE(FV_PROF_BICGSTAB, 1, launch_bicgstab(m, bp));
+    const int nl = 1 + prm->n_nonorth;
     for (int k = 0; k < prm->n_corr; ++k) {
         STAGE(FV_PROF_HBYA, 1, launch_hbya(c));
-        STAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
-        STAGE(FV_PROF_PCG, 1,
-              launch_pressure_solve(c, prm->p_tol, 0.0, prm->p_maxit, c->dstats + 3 + k));
+        for (int j = 0; j < nl; ++j) {
+            // non-orthogonal corrector: explicit term from the newest pressure
+            if (j > 0) STAGE(FV_PROF_PRESSURE, 1, launch_grad_p(c));
+            STAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
+            STAGE(FV_PROF_PCG, 1, launch_pressure_solve(c, prm->p_tol, 0.0, prm->p_maxit,
+                                                        c->dstats + 3 + k * nl + j));
+        }
         STAGE(FV_PROF_CORRECT, 1, launch_correct_piso(c));
     }
     return FV_OK;
@@ -142,6 +148,8 @@ fv_status check_piso(const fv_piso_params *prm)
     FV_CHECK(prm->dt > 0.0, FV_E_INVALID, "dt must be positive");
     FV_CHECK(prm->n_corr >= 1 && prm->n_corr <= FV_MAX_CORR, FV_E_INVALID,
              "n_corr must be in 1..%d", FV_MAX_CORR);
+    FV_CHECK(prm->n_nonorth >= 0 && prm->n_corr * (1 + prm->n_nonorth) <= FV_MAX_CORR,
+             FV_E_INVALID, "n_corr * (1 + n_nonorth) must be at most %d", FV_MAX_CORR);
     FV_CHECK(prm->p_maxit >= 0 && prm->u_maxit >= 0, FV_E_INVALID, "negative iteration limit");
     FV_CHECK(prm->p_tol >= 0.0 && prm->u_tol >= 0.0, FV_E_INVALID, "negative tolerance");
     return FV_OK;
@@ -337,11 +345,8 @@ static fv_status put_patch(fv_case *c, int q, const double *u_int /*[3][size] or
 extern "C" fv_status fv_patch_set_value(fv_case *c, int32_t q, const double u[3], double p)
 {
     FV_CHECK(c && q >= 0 && q < c->mesh->np, FV_E_INVALID, "bad patch index %d", q);
-    const size_t n = c->mesh->patches[q].size;
-    std::vector<double> uu(3 * n), pp(n, p);
-    for (int cc = 0; cc < 3; ++cc)
-        for (size_t j = 0; j < n; ++j) uu[cc * n + j] = u ? u[cc] : 0.0;
-    return put_patch(c, q, u ? uu.data() : nullptr, pp.data());
+    const fv_patch &pt = c->mesh->patches[q];
+    return launch_patch_fill(c, pt.start, pt.size, u, p);
 }
 
 extern "C" fv_status fv_patch_set_face_values(fv_case *c, int32_t q, const double *u, const double *p)
@@ -368,10 +373,10 @@ extern "C" fv_status fv_piso_step(fv_case *c, const fv_piso_params *prm, fv_step
     int ref = -1;
     if ((st = check_ref(c, prm->p_ref_cell, &ref)) != FV_OK) return st;
     if ((st = piso_enqueue(c, prm, ref)) != FV_OK) return st;
-    c->last_np = prm->n_corr;
+    c->last_np = prm->n_corr * (1 + prm->n_nonorth);
     c->last_simple = false;
     if (!stats) return FV_OK;
-    return read_stats(c, prm->n_corr, stats, false);
+    return read_stats(c, c->last_np, stats, false);
 }
 
 extern "C" fv_status fv_case_last_stats(fv_case *c, fv_step_stats *stats)
@@ -386,6 +391,8 @@ extern "C" fv_status fv_simple_iter(fv_case *c, const fv_simple_params *prm, fv_
     FV_CHECK(prm->alpha_u > 0.0 && prm->alpha_u <= 1.0 && prm->alpha_p > 0.0 && prm->alpha_p <= 1.0,
              FV_E_INVALID, "relaxation factors must be in (0, 1]");
     FV_CHECK(prm->p_maxit >= 0 && prm->u_maxit >= 0, FV_E_INVALID, "negative iteration limit");
+    FV_CHECK(prm->n_nonorth >= 0 && 1 + prm->n_nonorth <= FV_MAX_CORR, FV_E_INVALID,
+             "1 + n_nonorth must be at most %d", FV_MAX_CORR);
     const fv_mesh *m = c->mesh;
     int ref = -1;
     fv_status st = check_ref(c, prm->p_ref_cell, &ref);
@@ -401,13 +408,20 @@ extern "C" fv_status fv_simple_iter(fv_case *c, const fv_simple_params *prm, fv_
     STAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
     STAGE(FV_PROF_OTHER, 2, launch_simple_residuals_p(c));
     FV_CUDA(cudaMemcpyAsync(c->pold, c->p, sizeof(double) * m->N, cudaMemcpyDeviceToDevice, m->stream));
-    STAGE(FV_PROF_PCG, 1,
-          launch_pressure_solve(c, prm->p_tol, prm->p_reltol, prm->p_maxit, c->dstats + 3));
+    const int nl = 1 + prm->n_nonorth;
+    for (int j = 0; j < nl; ++j) {
+        if (j > 0) {
+            STAGE(FV_PROF_PRESSURE, 1, launch_grad_p(c));
+            STAGE(FV_PROF_PRESSURE, 1, launch_pressure(c, sa));
+        }
+        STAGE(FV_PROF_PCG, 1, launch_pressure_solve(c, prm->p_tol, prm->p_reltol, prm->p_maxit,
+                                                    c->dstats + 3 + j));
+    }
     STAGE(FV_PROF_CORRECT, 2, launch_correct_simple(c, prm->alpha_p));
-    c->last_np = 1;
+    c->last_np = nl;
     c->last_simple = true;
     if (!stats) return FV_OK;
-    return read_stats(c, 1, stats, true);
+    return read_stats(c, nl, stats, true);
 }
 
 extern "C" fv_status fv_piso_run_graph(fv_case *c, const fv_piso_params *prm, int32_t n_steps,
@@ -438,10 +452,10 @@ extern "C" fv_status fv_piso_run_graph(fv_case *c, const fv_piso_params *prm, in
         c->graph_prm = *prm;
     }
     for (int s = 0; s < n_steps; ++s) FV_CUDA(cudaGraphLaunch(c->graph, m->stream));
-    c->last_np = prm->n_corr;
+    c->last_np = prm->n_corr * (1 + prm->n_nonorth);
     c->last_simple = false;
     if (!stats) return FV_OK;
-    return read_stats(c, prm->n_corr, stats, false);
+    return read_stats(c, c->last_np, stats, false);
 }
 
 // ------------------------------------------------ stand-alone operators --

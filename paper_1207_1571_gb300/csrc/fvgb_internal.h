@@ -176,6 +176,7 @@ fv_status launch_grad_u(const fv_case *c);
 fv_status launch_momentum(const fv_case *c, const StepArgs &a);
 fv_status launch_hbya(const fv_case *c);
 fv_status launch_pressure(const fv_case *c, const StepArgs &a);
+fv_status launch_grad_p(const fv_case *c);
 fv_status launch_correct_piso(const fv_case *c);
 fv_status launch_correct_simple(const fv_case *c, double alpha_p);
 fv_status launch_simple_residuals_mom(const fv_case *c);
@@ -188,6 +189,7 @@ fv_status launch_ldu_to_sell(const fv_mesh *m, const double *upper, const double
 fv_status launch_permute_cells(const fv_mesh *m, int ncomp, const double *src, double *dst,
                                int to_internal);
 fv_status launch_permute_faces(const fv_mesh *m, const double *src, double *dst, int to_internal);
+fv_status launch_patch_fill(const fv_case *c, int start, int n, const double *u, double p);
 
 // krylov.cu
 struct CgProblem {

@@ -1,0 +1,60 @@
+"""Parity helpers shared by the GPU tests: the oracle's own sensitivity to
+rounding-sized input changes (the bar for long runs of a tolerance-
+truncated solver) and the checks made against it."""
+import numpy as np
+
+import oracle as O
+
+TOL = 1e-9
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def oracle_envelope(m, nu, nsteps, step, eps=1e-15, seeds=(1, 2)):
+    """Run the oracle from rest and from rest plus an eps-sized random
+    velocity perturbation; return the unperturbed case, its per-step
+    iteration counts, the per-step counts of the perturbed runs, and the
+    largest relative spread of each field at the end.  This is the oracle's
+    own sensitivity to rounding-sized changes of its input, the only honest
+    bar for a long run of a tolerance-truncated solver."""
+    def run(e, seed):
+        oc = O.Case(O.Mesh(m, renumber=True), nu)
+        if e > 0:
+            u = np.zeros((3, m.n_cells))
+            u[:2] = e * np.random.default_rng(seed).standard_normal((2, m.n_cells))
+            oc.set_fields(u, np.zeros(m.n_cells), np.zeros(m.n_faces))
+        its = [np.array(step(oc, n)["iters"]) for n in range(nsteps)]
+        return oc, np.array(its)
+    base, its0 = run(0.0, 0)
+    f0 = base.get_fields()
+    spread = np.zeros(3)
+    its_p = []
+    for sd in seeds:
+        oc, its = run(eps, sd)
+        its_p.append(its)
+        for k, a in enumerate(oc.get_fields()):
+            spread[k] = max(spread[k], rel(a, f0[k]))
+    return base, its0, its_p, spread
+
+
+def assert_in_envelope(case, base, spread, floor=TOL, factor=10.0):
+    got = case.get_fields_host()
+    ref = base.get_fields()
+    for k, name in enumerate(("u", "p", "phi")):
+        bar = max(floor, factor * spread[k])
+        assert rel(got[k], ref[k]) <= bar, (name, rel(got[k], ref[k]), bar)
+
+
+def assert_iters_where_well_conditioned(gpu_its, its0, its_p):
+    # compare only the solves whose count the perturbed oracle runs reproduce
+    stable = np.ones_like(its0, bool)
+    for its in its_p:
+        stable &= its == its0
+    gi = np.array(gpu_its)
+    bad = stable & (np.abs(gi - its0) > 1)
+    assert not bad.any(), (np.argwhere(bad)[:5], gi[bad][:5], its0[bad][:5])
+    return stable

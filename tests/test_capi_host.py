@@ -46,9 +46,42 @@ def test_struct_sizes_match_header(P):
     assert C.sizeof(_capi.fv_mesh_desc) == 80
     assert C.sizeof(_capi.fv_solve_stats) == 32
     assert C.sizeof(_capi.fv_step_stats) == 32 * 11 + 16
-    assert C.sizeof(_capi.fv_piso_params) == 48
+    assert C.sizeof(_capi.fv_piso_params) == 56
     assert C.sizeof(_capi.fv_simple_params) == 72
     assert C.sizeof(_capi.fv_pcg_params) == 24
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """Every ctypes field sits at the offset a C compiler gives it from the
+    header, and every struct has the header's size."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_1207_1571_gb300 import _capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [_capi.fv_patch, _capi.fv_mesh_desc, _capi.fv_solve_stats, _capi.fv_step_stats,
+               _capi.fv_piso_params, _capi.fv_simple_params, _capi.fv_pcg_params]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fvgb.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f in st._fields_:
+            lines.append(f'printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "sizeof")] == C.sizeof(st), n
+        for f in st._fields_:
+            assert got[(n, f[0])] == getattr(st, f[0]).offset, (n, f[0])
 
 
 MESHES = {
@@ -110,3 +143,37 @@ def test_rejects_patches_not_tiling(P):
     def f(m):
         m.patches[-1].size -= 1
     assert "patches" in _bad(P, f)
+
+
+# ------------------------------------------- hybrid ELL + J (paper Sec. 3.1) --
+
+def _ellj_equal(a, b):
+    for k in ("I", "J", "crs_ptr", "crs_col", "crs_tr"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_ellj_builder_worked_example(P):
+    from test_oracle_ellj import golden, example_pattern
+    I, J = golden()
+    rp, col = example_pattern()
+    e = P.ellj_build_host(rp, col, 3)
+    assert np.array_equal(e["I"], I) and np.array_equal(e["J"], J)
+
+
+@pytest.mark.parametrize("K", [2, 4, 5, 7, 8])
+@pytest.mark.parametrize("name", ["cube_perm", "tets", "cavity2d"])
+def test_ellj_builder_matches_oracle(P, name, K):
+    m = MESHES[name]()
+    om = O.Mesh(m, renumber=True)
+    own, nei = om.addressing()
+    rp, col = O.pattern_rows(m.n_cells, own, nei)
+    _ellj_equal(P.ellj_build_host(rp, col, K), O.ellj_build(rp, col, K))
+
+
+def test_ellj_builder_rejects_bad_patterns(P):
+    with pytest.raises(P.FvError):
+        P.ellj_build_host(np.array([0, 2, 3]), np.array([0, 1, 1]), 2)   # no transpose
+    with pytest.raises(P.FvError):
+        P.ellj_build_host(np.array([0, 2, 3]), np.array([1, 0, 1]), 2)   # unsorted row
+    with pytest.raises(P.FvError):
+        P.ellj_build_host(np.array([0, 1]), np.array([0]), 0)            # K = 0

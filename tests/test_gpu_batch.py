@@ -50,6 +50,28 @@ def test_batch_matches_oracle_case_by_case(P):
             assert rel(a, b) <= 1e-9, (k, name, rel(a, b))
 
 
+def test_batch_nonorth_correctors_mixed_meshes(P):
+    """Skewed tet boxes next to an orthogonal cavity in one batch, with one
+    non-orthogonal corrector per pressure corrector."""
+    a = mg.tet_box(4, 4, 4, jitter=0.15, seed=3)
+    a.patches[0].u = (1.0, 0.0, 0.3)
+    b = mg.tet_box(3, 5, 4, jitter=0.1, seed=4)
+    b.patches[0].u = (0.5, 0.2, 0.0)
+    cases = [(a, 0.05), (mg.cavity2d(12), 0.02), (b, 0.03)]
+    bt = P.Batch([m for m, _ in cases], [nu for _, nu in cases], [m.corner_cell for m, _ in cases])
+    ocs = [O.Case(O.Mesh(m, renumber=True), nu) for m, nu in cases]
+    for step in range(4):
+        st = bt.piso_step(0.01, 2, n_nonorth=1)
+        for k, oc in enumerate(ocs):
+            so = oc.piso_step(0.01, 2, p_ref_cell=cases[k][0].corner_cell, n_nonorth=1)
+            gi, oi = np.array(st[k]["iters"]), so["iters"]
+            assert st[k]["status"] == 0 and len(gi) == 3 + 4
+            assert np.abs(gi - oi).max() <= 1, (step, k, gi, oi)
+    for k, oc in enumerate(ocs):
+        for g, o, name in zip(bt.get_fields(k), oc.get_fields(), ("u", "p", "phi")):
+            assert rel(g, o) <= 1e-9, (k, name, rel(g, o))
+
+
 def test_batch_graph_and_schedules(P):
     cases = _cases()
     ms = [m for m, _ in cases]

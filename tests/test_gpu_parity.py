@@ -10,6 +10,7 @@ import pytest
 
 import meshgen as mg
 import oracle as O
+from parity_util import oracle_envelope, assert_in_envelope, assert_iters_where_well_conditioned
 
 pytestmark = pytest.mark.gpu
 
@@ -177,52 +178,6 @@ def test_bicgstab_matches_oracle(P, which):
 
 # -------------------------------------------------------------- PISO step --
 
-def oracle_envelope(m, nu, nsteps, step, eps=1e-15, seeds=(1, 2)):
-    """Run the oracle from rest and from rest plus an eps-sized random
-    velocity perturbation; return the unperturbed case, its per-step
-    iteration counts, the per-step counts of the perturbed runs, and the
-    largest relative spread of each field at the end.  This is the oracle's
-    own sensitivity to rounding-sized changes of its input, the only honest
-    bar for a long run of a tolerance-truncated solver."""
-    def run(e, seed):
-        oc = O.Case(O.Mesh(m, renumber=True), nu)
-        if e > 0:
-            u = np.zeros((3, m.n_cells))
-            u[:2] = e * np.random.default_rng(seed).standard_normal((2, m.n_cells))
-            oc.set_fields(u, np.zeros(m.n_cells), np.zeros(m.n_faces))
-        its = [np.array(step(oc)["iters"]) for _ in range(nsteps)]
-        return oc, np.array(its)
-    base, its0 = run(0.0, 0)
-    f0 = base.get_fields()
-    spread = np.zeros(3)
-    its_p = []
-    for sd in seeds:
-        oc, its = run(eps, sd)
-        its_p.append(its)
-        for k, a in enumerate(oc.get_fields()):
-            spread[k] = max(spread[k], rel(a, f0[k]))
-    return base, its0, its_p, spread
-
-
-def assert_in_envelope(case, base, spread, floor=TOL, factor=10.0):
-    got = case.get_fields_host()
-    ref = base.get_fields()
-    for k, name in enumerate(("u", "p", "phi")):
-        bar = max(floor, factor * spread[k])
-        assert rel(got[k], ref[k]) <= bar, (name, rel(got[k], ref[k]), bar)
-
-
-def assert_iters_where_well_conditioned(gpu_its, its0, its_p):
-    # compare only the solves whose count the perturbed oracle runs reproduce
-    stable = np.ones_like(its0, bool)
-    for its in its_p:
-        stable &= its == its0
-    gi = np.array(gpu_its)
-    bad = stable & (np.abs(gi - its0) > 1)
-    assert not bad.any(), (np.argwhere(bad)[:5], gi[bad][:5], its0[bad][:5])
-    return stable
-
-
 def test_piso_2d_cavity_40_steps_strict(P):
     """The 2-D lid-driven cavity workload (20x20, nu 0.1, dt 0.005, 2
     correctors, CG to 1e-6), 40 steps in lockstep with the oracle: iteration
@@ -245,7 +200,7 @@ def test_piso_2d_cavity_100_steps(P):
     stay within 10x the oracle's own spread, with iteration counts within 1
     wherever the perturbed oracle runs agree on them."""
     m = mg.cavity2d(20)
-    step = lambda c: c.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
+    step = lambda c, n: c.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
     base, its0, its_p, spread = oracle_envelope(m, 0.1, 100, step)
     mesh = P.Mesh(m, renumber=True)
     case = P.Case(mesh, 0.1)
@@ -259,7 +214,7 @@ def test_piso_2d_cavity_100_steps_fixed_iterations(P):
     """All 100 steps with the pressure CG fixed at 60 iterations per solve
     (tolerance 0) on both sides: no stopping decision at all."""
     m = mg.cavity2d(20)
-    step = lambda c: c.piso_step(0.005, 2, p_ref_cell=m.corner_cell, p_tol=0.0, p_maxit=60)
+    step = lambda c, n: c.piso_step(0.005, 2, p_ref_cell=m.corner_cell, p_tol=0.0, p_maxit=60)
     base, its0, its_p, spread = oracle_envelope(m, 0.1, 100, step)
     mesh = P.Mesh(m, renumber=True)
     case = P.Case(mesh, 0.1)
@@ -291,6 +246,56 @@ def test_piso_tets_nonorthogonal(P):
         so = oc.piso_step(0.01, 2, p_ref_cell=0)
         assert_iters(s, so)
     assert_fields(case, oc)
+
+
+@pytest.mark.parametrize("nn", [1, 3])
+def test_piso_tets_nonorth_correctors(P, nn):
+    """Non-orthogonal correctors (1 + nn pressure solves per corrector, the
+    explicit term re-evaluated from the newest pressure) on skewed tets."""
+    m = mg.tet_box(5, 5, 5, jitter=0.15, seed=3)
+    m.patches[0].u = (1.0, 0.0, 0.3)
+    mesh, case, om, oc = both(P, m, 0.05)
+    for step in range(4):
+        s = case.piso_step(0.02, 2, p_ref_cell=m.corner_cell, n_nonorth=nn)
+        so = oc.piso_step(0.02, 2, p_ref_cell=m.corner_cell, n_nonorth=nn)
+        assert s["status"] == 0 and len(s["p"]) == 2 * (1 + nn)
+        assert_iters(s, so)
+    assert_fields(case, oc)
+    # the same steps replayed from a CUDA graph
+    case.set_fields_host(np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_faces))
+    case.run_graph(4, 0.02, 2, p_ref_cell=m.corner_cell, n_nonorth=nn)
+    assert_fields(case, oc)
+
+
+def test_simple_tets_nonorth_correctors(P):
+    m = mg.duct_tets(3, 6)
+    F = m.n_internal_faces
+    inl = m.patches[m.patch("inlet")]
+    xy = m.Cf[:2, F + inl.start:F + inl.start + inl.size]
+    prof = mg.duct_inlet_profile(xy)
+    mesh, case, om, oc = both(P, m, 0.05)
+    for c in (case, oc):
+        c.set_patch_faces(m.patch("inlet"), np.stack([0 * prof, 0 * prof, prof]))
+    for it in range(10):
+        s = case.simple_iter(0.7, 0.3, n_nonorth=2)
+        so = oc.simple_iter(0.7, 0.3, n_nonorth=2)
+        assert len(s["p"]) == 3
+        assert_iters(s, so)
+        assert s["init_res_max"] == pytest.approx(so["init_res_max"], rel=1e-6)
+    assert_fields(case, oc)
+
+
+def test_nonorth_corrector_limits(P):
+    m = mg.cavity2d(4)
+    case = P.Case(P.Mesh(m), 0.1)
+    with pytest.raises(P.FvError):
+        case.piso_step(0.01, 2, p_ref_cell=0, n_nonorth=4)      # 2 x 5 > 8 solves
+    with pytest.raises(P.FvError):
+        case.piso_step(0.01, 2, p_ref_cell=0, n_nonorth=-1)
+    with pytest.raises(P.FvError):
+        case.simple_iter(p_ref_cell=0, n_nonorth=8)
+    s = case.piso_step(0.01, 4, p_ref_cell=0, n_nonorth=1)
+    assert len(s["p"]) == 8
 
 
 def test_piso_time_dependent_boundary_values(P):
@@ -388,10 +393,9 @@ def test_simple_channel_outlet(P):
     y = m.Cf[1, F + inl.start:F + inl.start + inl.size]
     prof = np.stack([6 * y * (1 - y), 0 * y, 0 * y])
 
-    def step(c):
-        if not getattr(c, "_inlet_set", False):
+    def step(c, n):
+        if n == 0:
             c.set_patch_faces(m.patch("inlet"), prof)
-            c._inlet_set = True
         return c.simple_iter(0.7, 0.3)
     base, its0, its_p, spread = oracle_envelope(m, 0.1, 30, step)
     mesh = P.Mesh(m, renumber=True)

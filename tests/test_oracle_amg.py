@@ -1,0 +1,179 @@
+"""Pins of the oracle's aggregation-multigrid preconditioned CG (the stronger
+pressure solver the paper's Sec. 5 and 6 ask for): the aggregation on hand
+examples and its invariants, the Galerkin coarse matrices against P^T A P,
+the V-cycle operator symmetric positive definite, exact on a single level,
+and the preconditioned CG against a dense solve, in far fewer iterations
+than Jacobi-CG."""
+import numpy as np
+import pytest
+
+import meshgen as mg
+import oracle as O
+
+
+def pressure_system(m, nu, dt, steps, ref, renumber=True):
+    om = O.Mesh(m, renumber=renumber)
+    oc = O.Case(om, nu)
+    for _ in range(steps):
+        oc.piso_step(dt, 2, p_ref_cell=ref)
+    return om, oc.pressure_system(dt, p_ref_cell=ref)
+
+
+def dense(n, ea, eb, d, o):
+    A = np.diag(np.asarray(d, float))
+    A[ea, eb] = o
+    A[eb, ea] = o
+    return A
+
+
+def test_chain_aggregates_by_fours():
+    """A 64-cell chain in natural order: the first pass pairs (0,1), (2,3),
+    ..., the second pairs those pairs; 16 aggregates of 4 consecutive cells,
+    which is <= 32 nodes, so that level is the coarsest."""
+    sp = {k: "w" for k in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")}
+    m = mg.hex_box(64, 1, 1, (64.0, 1.0, 1.0), sp, {"w": (mg.WALL, (0, 0, 0), 0.0)})
+    om = O.Mesh(m, renumber=False)
+    A = O.Amg(om)
+    n, ne = A.levels()
+    assert list(n) == [64, 16] and list(ne) == [63, 15]
+    agg, emap = A.maps(0)
+    assert np.array_equal(agg, np.arange(64) // 4)
+    expect = np.full(63, -1)
+    expect[3::4] = np.arange(15)          # the face between cells 4k+3 and 4k+4
+    assert np.array_equal(emap, expect)
+    ea, eb = A.edges(1)
+    assert np.array_equal(ea, np.arange(15)) and np.array_equal(eb, np.arange(1, 16))
+
+
+def test_anisotropic_cells_pair_along_the_strong_direction():
+    """Cells 1 wide and 10 high: |S| Delta is 100x larger across the x
+    faces, so every aggregate is a run of 4 cells within one row."""
+    sp = {k: "w" for k in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")}
+    m = mg.hex_box(40, 4, 1, (40.0, 40.0, 1.0), sp, {"w": (mg.WALL, (0, 0, 0), 0.0)})
+    om = O.Mesh(m, renumber=False)
+    agg, _ = O.Amg(om).maps(0)
+    i, j = np.arange(160) % 40, np.arange(160) // 40
+    for a in np.unique(agg):
+        cells = np.nonzero(agg == a)[0]
+        assert len(set(j[cells])) == 1 and len(cells) == 4
+        assert np.ptp(i[cells]) == 3
+
+
+@pytest.mark.parametrize("maker", [lambda: mg.permute_cells(mg.cavity3d(12), mg.random_permutation(1728, 3)),
+                                   lambda: mg.duct_tets(6, 12),
+                                   lambda: mg.tp_channel(160, 15)])
+def test_hierarchy_invariants(maker):
+    m = maker()
+    om = O.Mesh(m, renumber=True)
+    A = O.Amg(om)
+    n, ne = A.levels()
+    assert n[-1] <= 32 and (np.diff(n) < 0).all()
+    for l in range(len(n) - 1):
+        agg, emap = A.maps(l)
+        ea, eb = A.edges(l)
+        # a partition onto 0..n[l+1]-1, every aggregate used
+        assert agg.min() == 0 and agg.max() == n[l + 1] - 1
+        assert len(np.unique(agg)) == n[l + 1]
+        # the coarse edges are exactly the aggregate pairs joined by a fine edge
+        ca, cb = agg[ea], agg[eb]
+        cross = ca != cb
+        assert np.array_equal(emap < 0, ~cross)
+        pairs = sorted(set(zip(np.minimum(ca, cb)[cross], np.maximum(ca, cb)[cross])))
+        cea, ceb = A.edges(l + 1)
+        assert list(zip(cea, ceb)) == pairs
+        assert (cea[emap[cross]] == np.minimum(ca, cb)[cross]).all()
+        # aggregates are connected through edges inside them
+        parent = np.arange(n[l])
+
+        def find(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+        for a, b in zip(ea[~cross], eb[~cross]):
+            parent[find(a)] = find(b)
+        roots = np.array([find(x) for x in range(n[l])])
+        for a in range(n[l + 1]):
+            assert len(set(roots[agg == a])) == 1
+
+
+def test_galerkin_coarse_matrices_equal_ptap():
+    m = mg.permute_cells(mg.cavity3d(8), mg.random_permutation(512, 9))
+    om, (d, up, b) = pressure_system(m, 0.01, 0.01, 2, m.corner_cell)
+    A = O.Amg(om)
+    A.vcycle(d, up, b)
+    n, ne = A.levels()
+    for l in range(len(n) - 1):
+        agg, _ = A.maps(l)
+        df, of = A.matrix(l)
+        ea, eb = A.edges(l)
+        Af = dense(n[l], ea, eb, df, of)
+        Pm = np.zeros((n[l], n[l + 1]))
+        Pm[np.arange(n[l]), agg] = 1.0
+        dc, oc = A.matrix(l + 1)
+        cea, ceb = A.edges(l + 1)
+        assert np.allclose(dense(n[l + 1], cea, ceb, dc, oc), Pm.T @ Af @ Pm, rtol=1e-13,
+                           atol=1e-13 * np.abs(Af).max())
+
+
+def test_vcycle_is_symmetric_positive_definite():
+    m = mg.tet_box(4, 4, 4, jitter=0.1)
+    m.patches[0].u = (1.0, 0.0, 0.2)
+    om, (d, up, b) = pressure_system(m, 0.05, 0.02, 2, m.corner_cell)
+    A = O.Amg(om)
+    n, _ = A.levels()
+    assert len(n) >= 3
+    M = np.stack([A.vcycle(d, up, e) for e in np.eye(len(d))], axis=1)
+    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+    # and it is a good approximate inverse: the preconditioned spectrum is
+    # clustered (condition number far below Jacobi's)
+    own, nei = om.addressing()
+    Ad = dense(len(d), own[:len(up)], nei, d, up)
+    ev = np.sort(np.linalg.eigvals(M @ Ad).real)
+    ej = np.sort(np.linalg.eigvals(Ad / d[:, None]).real)
+    assert ev[-1] / ev[0] < 0.1 * ej[-1] / ej[0]
+
+
+def test_single_level_is_the_exact_solve():
+    m = mg.cavity2d(5)                      # 25 cells <= 32: the coarsest level only
+    om, (d, up, b) = pressure_system(m, 0.1, 0.005, 3, m.corner_cell, renumber=False)
+    A = O.Amg(om)
+    assert len(A.levels()[0]) == 1
+    own, nei = om.addressing()
+    x = np.linalg.solve(dense(25, own[:len(up)], nei, d, up), b)
+    assert np.abs(A.vcycle(d, up, b) - x).max() <= 1e-13 * np.abs(x).max()
+    xs, it, r0, r1, st = A.pcg(d, up, b, np.zeros(25), tol=1e-12)
+    assert st == 0 and it == 1
+
+
+@pytest.mark.parametrize("which", ["cavity", "tets", "channel"])
+def test_amg_pcg_against_dense_and_jacobi(which):
+    if which == "cavity":
+        m = mg.permute_cells(mg.cavity3d(9), mg.random_permutation(729, 4))
+        om, (d, up, b) = pressure_system(m, 0.01, 0.01, 2, m.corner_cell)
+    elif which == "tets":
+        m = mg.tet_box(5, 4, 4, jitter=0.1)
+        m.patches[0].u = (0.5, 0.0, 0.2)
+        om, (d, up, b) = pressure_system(m, 0.05, 0.02, 2, m.corner_cell)
+    else:
+        m = mg.tp_channel(120, 12)
+        om = O.Mesh(m, renumber=True)
+        oc = O.Case(om, 3.3e-6)
+        oc.set_patch(m.patch("inlet"), mg.tp_inlet(1e-4), 0.0)
+        oc.piso_step(1e-4, 2)
+        oc.set_patch(m.patch("inlet"), mg.tp_inlet(2e-4), 0.0)
+        d, up, b = oc.pressure_system(1e-4)
+    own, nei = om.addressing()
+    xd = np.linalg.solve(dense(len(d), own[:len(up)], nei, d, up), b)
+    A = O.Amg(om)
+    x, it, r0, r1, st = A.pcg(d, up, b, np.zeros(len(d)), tol=1e-12)
+    assert st == 0 and r1 <= 1e-12
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    _, itj, _, _, _ = O.pcg(own, nei, d, up, b, np.zeros(len(d)), tol=1e-12)
+    assert it < 0.3 * itj, (it, itj)
+    # the stopping rule is orc_pcg's: zero rhs and iteration limit
+    x, it, r0, r1, st = A.pcg(d, up, 0 * b, np.ones(len(d)))
+    assert it == 0 and st == 0 and not x.any()
+    x, it, r0, r1, st = A.pcg(d, up, b, np.zeros(len(d)), tol=1e-14, maxit=2)
+    assert st == -1 and it == 2

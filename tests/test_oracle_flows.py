@@ -3,7 +3,8 @@ closed-form flows and exact identities: mass conservation after every
 pressure correction, plane Couette flow (reproduced exactly by central
 differencing), plane Poiseuille flow (second-order convergence to the
 parabola), Taylor-Green vortex decay with time-dependent boundary values
-(Sec. 1/6: time-dependent boundary conditions), the rectangular-duct series
+(Sec. 1/6: time-dependent boundary conditions), transient Poiseuille flow
+started by a sinusoidal inlet (exact start-up solution), the rectangular-duct series
 solution, and the mirror symmetry of the 3-D lid-driven cavity."""
 import numpy as np
 import pytest
@@ -220,6 +221,118 @@ def test_taylor_green_decay():
     assert e64[2] == pytest.approx(e64[3], rel=1e-3)
     assert e32[2] == pytest.approx(e32[3], rel=1e-2)
     assert e64[0] < 2e-4
+
+
+# ---------------------------------------------------------------------------
+# non-orthogonal correctors: the pressure equation re-solved with the
+# explicit non-orthogonal term evaluated from the newest pressure
+# ---------------------------------------------------------------------------
+
+def test_nonorth_correctors_contract_on_skewed_tets():
+    """Each extra loop starts from the defect left by re-evaluating the
+    explicit term at the new pressure; the loops are a contraction, so
+    those initial residuals fall geometrically, and the flux correction
+    (made with the last loop's term) satisfies the continuity identity."""
+    m = mg.tet_box(5, 5, 5, jitter=0.15, seed=3)
+    m.patches[0].u = (1.0, 0.0, 0.3)
+    cs = O.Case(O.Mesh(m, renumber=True), 0.05)
+    nn = 4
+    for _ in range(3):
+        st = cs.piso_step(0.02, 2, p_ref_cell=m.corner_cell, n_nonorth=nn, p_tol=1e-10)
+        assert st["status"] == 0 and st["cont_err"] < 1e-12
+        assert len(st["iters"]) == 3 + 2 * (nn + 1)
+        r0 = st["res0"][3:].reshape(2, nn + 1)
+        for k in range(2):
+            assert (r0[k, 2:] < 0.6 * r0[k, 1:-1]).all(), r0
+
+
+def test_nonorth_correctors_are_no_ops_on_orthogonal_meshes():
+    m = mg.cavity2d(20)
+    out = {}
+    for nn in (0, 2):
+        cs = O.Case(O.Mesh(m), 0.1)
+        for _ in range(10):
+            st = cs.piso_step(0.005, 2, p_ref_cell=m.corner_cell, n_nonorth=nn)
+        if nn:
+            assert (st["iters"][3:].reshape(2, 3)[:, 1:] == 0).all()
+        out[nn] = cs.get_fields()
+    for a, b in zip(out[0], out[2]):
+        assert np.array_equal(a, b)
+
+
+def test_nonorth_correctors_keep_the_simple_fixed_point():
+    """At the converged SIMPLE state the pressure already satisfies the
+    equation with its own explicit term, so the steady solution does not
+    depend on the number of non-orthogonal correctors."""
+    m = mg.duct_tets(3, 6)
+    xy = patch_face_centres(m, "inlet")[:2]
+    prof = mg.duct_inlet_profile(xy)
+    out = {}
+    for nn in (0, 2):
+        cs = O.Case(O.Mesh(m, renumber=True), 0.05)
+        cs.set_patch_faces(m.patch("inlet"), np.stack([0 * prof, 0 * prof, prof]))
+        for it in range(3000):
+            st = cs.simple_iter(0.7, 0.3, n_nonorth=nn, p_tol=1e-12, p_reltol=0.01)
+            assert len(st["iters"]) == 4 + nn
+            if st["init_res_max"] < 1e-10:
+                break
+        assert st["init_res_max"] < 1e-10
+        out[nn] = cs.get_fields()
+    for a, b in zip(out[0], out[2]):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(a)
+
+
+# ---------------------------------------------------------------------------
+# transient Poiseuille flow (the paper's tp1M case, Sec. 4.1): a channel
+# started from rest by a sinusoidal uniform inlet velocity
+# ---------------------------------------------------------------------------
+
+def _startup_channel(ny, nsteps, T=0.5, H=1.0, L=8.0, nu=0.05, u0=1.0, w=np.pi):
+    """Oracle PISO run with the inlet value set to u0 sin(w t_{n+1}) before
+    every step; returns the mid-channel profile error against the exact
+    start-up solution, the pressure-gradient error, and max |v|."""
+    from womersley import StartupChannel
+    nx = int(L / H * ny / 2)
+    m = mg.channel2d(nx, ny, L, H, inlet_u=(0.0, 0.0, 0.0))
+    cs = O.Case(O.Mesh(m), nu)
+    q = m.patch("inlet")
+    dt = T / nsteps
+    for n in range(nsteps):
+        cs.set_patch(q, (u0 * np.sin(w * (n + 1) * dt), 0.0, 0.0), 0.0)
+        st = cs.piso_step(dt, 2)
+        assert st["status"] == 0 and st["cont_err"] < 1e-12
+    u, p, phi = cs.get_fields()
+    S = StartupChannel(H, nu, u0, w)
+    i = np.arange(m.n_cells) % nx
+    a, b = nx // 2 - 1, nx // 2
+    y = m.C[1][i == a]
+    ue = S.u(y, T)
+    eu = np.linalg.norm(u[0][i == a] - ue) / np.linalg.norm(ue)
+    G = -(p[i == b] - p[i == a]).mean() / (L / nx)
+    eg = abs(G - S.G(T)) / abs(S.G(T))
+    # the inlet delivers Q(T) and the outlet takes it out
+    F = m.n_internal_faces
+    inl, out = m.patches[q], m.patches[m.patch("outlet")]
+    dz = m.V[0] / (L / nx * H / ny)
+    qin = -phi[F + inl.start:F + inl.start + inl.size].sum() / dz
+    qout = phi[F + out.start:F + out.start + out.size].sum() / dz
+    assert qin == pytest.approx(S.Q(T), rel=1e-12)
+    assert qout == pytest.approx(qin, rel=1e-5)
+    return eu, eg, np.abs(u[1][i == a]).max()
+
+
+def test_transient_poiseuille_startup_converges():
+    """Womersley number 4 (H = 1, nu = 0.05, w = pi) to a quarter period:
+    the velocity profile far from both ends converges at second order to
+    the exact start-up solution; the pressure gradient at first order (the
+    wall shear from the half-cell distance is first order); the flow there
+    is parallel."""
+    e8, e16, e32 = _startup_channel(8, 25), _startup_channel(16, 50), _startup_channel(32, 100)
+    assert e8[0] / e16[0] > 3.5 and e16[0] / e32[0] > 3.5, (e8, e16, e32)
+    assert e32[0] < 3e-3
+    assert e8[1] / e16[1] > 1.7 and e16[1] / e32[1] > 1.7, (e8, e16, e32)
+    assert e32[1] < 0.05
+    assert max(e8[2], e16[2], e32[2]) < 1e-6
 
 
 # ---------------------------------------------------------------------------
