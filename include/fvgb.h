@@ -331,6 +331,46 @@ fv_status fv_bicgstab_solve(const fv_mesh *mesh, const double *diag, const doubl
                             const double *lower, const double *b, double *x,
                             const fv_pcg_params *prm, fv_solve_stats *stats);
 
+/* ---------------------------------------------- multigrid pressure CG -- */
+/* CG preconditioned by one aggregation-multigrid V-cycle: the stronger
+ * pressure solver the paper's discussion (Sec. 5 and 6) calls for, where
+ * its GPU code uses Jacobi-CG and its CPU comparison uses OpenFOAM's GAMG.
+ * Hierarchy (once per mesh, host, from the geometry): level 0 is the cell
+ * graph weighted by |S_f| Delta_f; each level comes from two pairwise-
+ * matching passes; coarsening stops at <= 32 nodes.  Per solve (device):
+ * Galerkin coarse matrices P^T A P with piecewise-constant P, the coarsest
+ * factored by Cholesky; the V-cycle smooths with two weighted-Jacobi sweeps
+ * (omega 2/3) before and after the coarse correction, which is added with
+ * the over-correction factor 1.8 (keeps the cycle SPD).  The CG's stopping
+ * rule, warm start and statistics are those of fv_pcg_solve. */
+typedef enum { FV_PSOLVER_JACOBI = 0, FV_PSOLVER_AMG = 1 } fv_pressure_solver;
+
+/* Symmetric A (diag [N], upper [F], device, the mesh's internal order).
+ * The first call on a mesh builds the hierarchy (synchronous; later calls
+ * reuse it).  Errors: FV_E_INVALID (arguments), FV_E_UNSUPPORTED (the
+ * coarsening stalls above 64 nodes, e.g. a graph of isolated cells),
+ * FV_E_NOT_CONVERGED / FV_E_DIVERGED as fv_pcg_solve (DIVERGED also when a
+ * coarse matrix is not positive definite). */
+fv_status fv_pcg_solve_amg(const fv_mesh *mesh, const double *diag, const double *upper,
+                           const double *b, double *x, const fv_pcg_params *prm,
+                           fv_solve_stats *stats);
+/* Build the hierarchy if needed; *n_levels and, if sizes is not NULL, the
+ * node count of every level (sizes [n_levels], at most 24). */
+fv_status fv_amg_info(const fv_mesh *mesh, int32_t *n_levels, int32_t *sizes);
+/* Pressure solver of a case's PISO steps and SIMPLE iterations (default
+ * FV_PSOLVER_JACOBI).  Selecting FV_PSOLVER_AMG builds the mesh's
+ * hierarchy now (synchronous), so later steps may be captured in graphs;
+ * FV_E_UNSUPPORTED for mixed-precision cases. */
+fv_status fv_case_set_pressure_solver(fv_case *cs, int32_t solver);
+/* Host only (no GPU): one coarsening level of a graph of n nodes and ne
+ * edges (ea < eb, ordered by (ea, eb), weights ew > 0): agg [n] (node ->
+ * aggregate), emap [ne] (edge -> coarse edge, -1 inside an aggregate), the
+ * coarse graph in cea, ceb, cew (capacity ne) with *n_coarse nodes and
+ * *ne_coarse edges.  FV_E_INVALID for malformed graphs. */
+fv_status fv_amg_coarsen_host(int32_t n, int32_t ne, const int32_t *ea, const int32_t *eb,
+                              const double *ew, int32_t *agg, int32_t *emap, int32_t *n_coarse,
+                              int32_t *ne_coarse, int32_t *cea, int32_t *ceb, double *cew);
+
 /* ------------------------------------------------------------ kernels -- */
 
 /* Gauss gradient of a cell field (Sec. 4.3.3): grad x_P = (1/V_P) sum_f S_f

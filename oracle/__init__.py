@@ -100,6 +100,8 @@ def lib():
             L.orc_laplacian_system.argtypes = [vp, _f64p, vp, _f64p, _f64p, _f64p]
             L.orc_ellj_build.argtypes = [C.c_int, _i32p, _i32p, C.c_int, vp, vp, _i32p, vp, vp]
             L.orc_ellj_build.restype = C.c_int
+            L.orc_case_set_pressure_solver.argtypes = [vp, C.c_int]
+            L.orc_case_set_pressure_solver.restype = C.c_int
             L.orc_amg_new.restype = vp
             L.orc_amg_new.argtypes = [vp]
             L.orc_amg_free.argtypes = [vp]
@@ -283,6 +285,11 @@ class Case:
                                    C.byref(ce), C.byref(irm))
         return dict(status=st, iters=its, res0=res[0::2], res=res[1::2], cont_err=ce.value,
                     init_res_max=irm.value)
+
+    def set_pressure_solver(self, solver):
+        """0: Jacobi-CG (default), 1: aggregation-multigrid preconditioned CG."""
+        if lib().orc_case_set_pressure_solver(self.h, solver) != 0:
+            raise ValueError(f"unknown pressure solver {solver}")
 
     def momentum_system(self, transient=True, dt=1.0, alpha_u=1.0):
         m = self.mesh

@@ -56,12 +56,22 @@ typedef struct {
     signed char *flipped;
 } omesh;
 
+struct oamg_s;
+
 typedef struct {
     omesh *m;
     double nu;
     double *u, *p, *phi;    /* [3N], [N], [F+B] */
     double *ub, *pb;        /* boundary-face values [3B], [B] */
+    int psolver;            /* pressure solver: 0 Jacobi-CG, 1 multigrid-CG */
+    struct oamg_s *amg;     /* multigrid hierarchy (built when selected) */
 } ocase;
+
+struct oamg_s *orc_amg_new(const omesh *m);
+void orc_amg_free(struct oamg_s *h);
+int orc_amg_pcg(struct oamg_s *h, const double *diag, const double *upper, const double *b,
+                double *x, double tol, double reltol, int maxit, double *res0_out,
+                double *res_out, int *iters_out);
 
 /* ------------------------------------------------------------------------ */
 /* small vector helpers (sequential)                                         */
@@ -524,6 +534,7 @@ void orc_case_free(ocase *cs)
 {
     if (!cs) return;
     free(cs->u); free(cs->p); free(cs->phi); free(cs->ub); free(cs->pb);
+    orc_amg_free(cs->amg);
     free(cs);
 }
 
@@ -917,6 +928,28 @@ static void correct_velocity(ocase *cs, const pwork *w, double *gradp)
             cs->u[c * N + i] = w->HbyA[c * N + i] - w->rAU[i] * gradp[c * N + i];
 }
 
+/* The pressure solve of a corrector: Jacobi-CG, or CG preconditioned by   */
+/* the aggregation-multigrid V-cycle when the case selects it.               */
+static int pressure_solve(ocase *cs, const pwork *w, double tol, double reltol, int maxit,
+                          double *res0, double *res1, int *iters)
+{
+    const omesh *m = cs->m;
+    if (cs->psolver == 1)
+        return orc_amg_pcg(cs->amg, w->pdiag, w->pup, w->pb, cs->p, tol, reltol, maxit, res0,
+                           res1, iters);
+    return orc_pcg(m->N, m->F, m->own, m->nei, w->pdiag, w->pup, w->pb, cs->p, tol, reltol,
+                   maxit, res0, res1, iters);
+}
+
+/* select the pressure solver: 0 Jacobi-CG, 1 multigrid-CG */
+int orc_case_set_pressure_solver(ocase *cs, int solver)
+{
+    if (solver != 0 && solver != 1) return -1;
+    if (solver == 1 && !cs->amg) cs->amg = orc_amg_new(cs->m);
+    cs->psolver = solver;
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* PISO time step (paper Sec. 3): momentum predictor, then n_corr pressure   */
 /* corrections.  M is assembled once per step; H uses the current u.         */
@@ -964,8 +997,8 @@ int orc_piso_step(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol,
             const int sk = 3 + k * (n_nonorth + 1) + j;
             if (j > 0) grad_p(cs, cs->p, gradp);
             assemble_pressure(cs, gradp, ref, p_ref, &w);
-            st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, 0.0, p_maxit,
-                         &res[2 * sk], &res[2 * sk + 1], &iters[sk]);
+            st = pressure_solve(cs, &w, p_tol, 0.0, p_maxit, &res[2 * sk], &res[2 * sk + 1],
+                                &iters[sk]);
             if (st && !status) status = st;
         }
         correct_flux(cs, &w);
@@ -1040,8 +1073,8 @@ int orc_simple_iter(ocase *cs, double alpha_u, double alpha_p, int n_nonorth, do
             grad_p(cs, cs->p, gradp);
             assemble_pressure(cs, gradp, ref, p_ref, &w);
         }
-        st = orc_pcg(N, F, m->own, m->nei, w.pdiag, w.pup, w.pb, cs->p, p_tol, p_reltol, p_maxit,
-                     &res[2 * (3 + j)], &res[2 * (3 + j) + 1], &iters[3 + j]);
+        st = pressure_solve(cs, &w, p_tol, p_reltol, p_maxit, &res[2 * (3 + j)],
+                            &res[2 * (3 + j) + 1], &iters[3 + j]);
         if (st && !status) status = st;
     }
     correct_flux(cs, &w);
@@ -1230,7 +1263,7 @@ int orc_ellj_build(int n, const int *row_ptr, const int *col, int K, int *I, int
 #define AMG_NMIN 32
 #define AMG_TIE 1e-9
 
-typedef struct {
+typedef struct oamg_s {
     int nlev;
     int n[AMG_MAXLEV], ne[AMG_MAXLEV];
     int *ea[AMG_MAXLEV], *eb[AMG_MAXLEV];    /* edges of level l, ea < eb */

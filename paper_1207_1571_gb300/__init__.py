@@ -19,10 +19,10 @@ from typing import Optional
 import numpy as np
 
 from . import _capi
-from ._capi import (FV_PREC_FP64, FV_PREC_MIXED, FV_E_NOT_CONVERGED, FV_OK, FvError,  # noqa
+from ._capi import (FV_PREC_FP64, FV_PREC_MIXED, FV_PSOLVER_JACOBI, FV_PSOLVER_AMG, FV_E_NOT_CONVERGED, FV_OK, FvError,  # noqa
                     check, load)
 
-__all__ = ["Mesh", "Case", "Batch", "Ellj", "mesh_plan", "ellj_build_host", "load", "FvError", "FV_PREC_FP64",
+__all__ = ["Mesh", "Case", "Batch", "Ellj", "mesh_plan", "ellj_build_host", "amg_coarsen_host", "load", "FvError", "FV_PREC_FP64",
            "FV_PREC_MIXED"]
 
 
@@ -170,6 +170,24 @@ class Mesh:
         check(rc, "fv_pcg_solve_mixed", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
         return _solve_dict(st)
 
+    def pcg_solve_amg(self, diag, upper, b, x, tol=1e-6, reltol=0.0, maxit=10000) -> dict:
+        """Aggregation-multigrid preconditioned CG (fv_pcg_solve_amg)."""
+        prm = _capi.fv_pcg_params(tol, reltol, maxit, 0)
+        st = _capi.fv_solve_stats()
+        self._enter(diag, upper, b, x)
+        rc = self.L.fv_pcg_solve_amg(self.h, diag.data_ptr(), _ptr(upper), b.data_ptr(),
+                                     x.data_ptr(), C.byref(prm), C.byref(st))
+        self._leave()
+        check(rc, "fv_pcg_solve_amg", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
+        return _solve_dict(st)
+
+    def amg_levels(self) -> list:
+        """Node count of every level of the multigrid hierarchy."""
+        n = C.c_int32()
+        sizes = np.zeros(32, np.int32)
+        check(self.L.fv_amg_info(self.h, C.byref(n), sizes.ctypes.data), "fv_amg_info")
+        return [int(v) for v in sizes[:n.value]]
+
     def bicgstab_solve(self, diag, upper, lower, b, x, tol=1e-10, reltol=0.0, maxit=1000) -> dict:
         prm = _capi.fv_pcg_params(tol, reltol, maxit, 0)
         st = _capi.fv_solve_stats()
@@ -216,6 +234,27 @@ def ellj_build_host(row_ptr, col, K: int) -> dict:
                                J.ctypes.data, crs_ptr.ctypes.data, crs_col.ctypes.data,
                                crs_tr.ctypes.data, C.byref(ncrs)), "fv_ellj_build_host")
     return dict(I=I, J=J, crs_ptr=crs_ptr, crs_col=crs_col[:ncrs.value], crs_tr=crs_tr[:ncrs.value])
+
+
+def amg_coarsen_host(n, ea, eb, ew) -> dict:
+    """Host-only multigrid coarsening level (``fv_amg_coarsen_host``):
+    agg, emap and the coarse graph (n, a, b, w).  Touches no GPU."""
+    L = load()
+    ea = np.ascontiguousarray(ea, dtype=np.int32)
+    eb = np.ascontiguousarray(eb, dtype=np.int32)
+    ew = np.ascontiguousarray(ew, dtype=np.float64)
+    ne = len(ea)
+    agg = np.zeros(max(n, 1), np.int32)
+    emap = np.zeros(max(ne, 1), np.int32)
+    cea = np.zeros(max(ne, 1), np.int32); ceb = np.zeros(max(ne, 1), np.int32)
+    cew = np.zeros(max(ne, 1))
+    nc, nec = C.c_int32(), C.c_int32()
+    check(L.fv_amg_coarsen_host(n, ne, ea.ctypes.data, eb.ctypes.data, ew.ctypes.data,
+                                agg.ctypes.data, emap.ctypes.data, C.byref(nc), C.byref(nec),
+                                cea.ctypes.data, ceb.ctypes.data, cew.ctypes.data),
+          "fv_amg_coarsen_host")
+    k = nec.value
+    return dict(agg=agg[:n], emap=emap[:ne], n=nc.value, a=cea[:k], b=ceb[:k], w=cew[:k])
 
 
 class Ellj:
@@ -329,6 +368,10 @@ class Case:
         d = np.load(path)
         self.set_fields_host(d["u"], d["p"], d["phi"])
         return {k: d[k] for k in d.files if k not in ("u", "p", "phi", "nu")}
+
+    def set_pressure_solver(self, solver: int):
+        """FV_PSOLVER_JACOBI (default) or FV_PSOLVER_AMG."""
+        check(self.L.fv_case_set_pressure_solver(self.h, solver), "fv_case_set_pressure_solver")
 
     def set_patch(self, q: int, u=(0.0, 0.0, 0.0), p: float = 0.0):
         uu = np.ascontiguousarray(u, dtype=np.float64)

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "FV_OK", 1: "FV_E_INVALID", 2: "FV_E_CUDA", 3: "FV_E_NOMEM",
                 7: "FV_E_UNSUPPORTED"}
 FV_PATCH_WALL, FV_PATCH_INLET, FV_PATCH_OUTLET, FV_PATCH_EMPTY = range(4)
 FV_PREC_FP64, FV_PREC_MIXED = 0, 1
+FV_PSOLVER_JACOBI, FV_PSOLVER_AMG = 0, 1
 FV_MAX_CORR = 8
 
 EXPORTS = [
@@ -30,7 +31,8 @@ EXPORTS = [
     "fv_pcg_solve_mixed", "fv_batch_create", "fv_batch_destroy", "fv_batch_piso_step",
     "fv_batch_run_graph", "fv_batch_get_fields", "fv_batch_schedule_info", "fv_batch_set_schedule",
     "fv_batch_autotune", "fv_ellj_build_host", "fv_ellj_create", "fv_ellj_destroy", "fv_ellj_info",
-    "fv_ellj_from_ldu", "fv_ellj_spmv",
+    "fv_ellj_from_ldu", "fv_ellj_spmv", "fv_pcg_solve_amg", "fv_amg_info",
+    "fv_case_set_pressure_solver", "fv_amg_coarsen_host",
 ]
 PROF_STAGES = ["momentum", "bicgstab", "hbya", "pressure", "pcg", "correct", "other"]
 
@@ -131,6 +133,10 @@ def load(path: str = LIB_PATH):
         "fv_ellj_info": [vp, vp, vp],
         "fv_ellj_from_ldu": [vp, vp, vp, vp, vp, vp],
         "fv_ellj_spmv": [vp, vp, vp, vp, vp, i32],
+        "fv_pcg_solve_amg": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
+        "fv_amg_info": [vp, vp, vp],
+        "fv_case_set_pressure_solver": [vp, i32],
+        "fv_amg_coarsen_host": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "fv_set_barrier_spin_limit": [C.c_int64],
         "fv_case_memory": [vp, P(C.c_int64)],
         "fv_profile_enable": [i32],

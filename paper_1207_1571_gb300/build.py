@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfvgb.so")
 SOURCES = ["mesh_plan.cpp", "mesh.cu", "assembly.cu", "krylov.cu", "case.cu", "profile.cu", "noalloc.cu",
-           "batch.cu", "ellj.cu"]
+           "batch.cu", "ellj.cu", "amg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,783 @@
+// amg.cu -- aggregation-multigrid preconditioned CG for the pressure
+// equation: the stronger pressure solver the paper's discussion (Sec. 5,
+// Sec. 6) names as the way past Jacobi-CG, built for one GB300.
+//
+// Setup, once per mesh (host): a hierarchy of aggregates from the geometry
+// alone.  Level 0 is the cell graph with edge weights |S_f| Delta_f; each
+// level's aggregates come from two pairwise-matching passes (a node is
+// paired with its unassigned neighbour of largest weight, or joins its
+// strongest neighbour's aggregate when all are taken; weights within a
+// relative 1e-9 tie and the lower index wins); the coarse graph joins two
+// aggregates that share an edge, with summed weight, edges ordered by
+// (lower, higher) aggregate.  Coarsening stops at <= 32 nodes or when a
+// level shrinks by less than 10 %.
+//
+// Per solve (device, one cooperative launch): Galerkin coarse matrices
+// A_c = P^T A P for piecewise-constant P (coarse diagonal = members'
+// diagonals + twice the coefficients of the edges inside the aggregate;
+// coarse edge = sum of its fine edges; every sum in ascending fine index),
+// the coarsest matrix factored by Cholesky, then CG preconditioned by one
+// V-cycle: per level two weighted-Jacobi sweeps (omega = 2/3) from zero,
+// the residual summed over each aggregate, the coarse correction added with
+// the over-correction factor 1.8, two sweeps again.
+//
+// GB300 mapping: levels with many rows run over the whole grid with the
+// bounded grid barrier between dependent phases; the small levels (and the
+// coarsest solve) run inside block 0 with block barriers only, while the
+// other blocks wait at the next grid barrier.  Pre-smoothing's first sweep
+// is fused into the phase that produces the level's right-hand side, the
+// residual into the restriction, and the prolongation into the first
+// post-smoothing sweep, so a grid level costs four grid barriers per cycle.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fvgb_internal.h"
+#include "coop.cuh"
+
+namespace fvgb {
+
+constexpr int kAmgMaxLev = 24;
+constexpr int kAmgNmin = 32;           // coarsest level size target
+constexpr int kAmgCoarseMax = 64;      // largest coarsest level handled on the device
+constexpr int kAmgBlock = 512;
+constexpr int kAmgBlockRows = 8192;    // levels up to this size run inside block 0
+constexpr double kAmgTie = 1e-9;
+constexpr double kAmgOmega = 2.0 / 3.0;
+constexpr double kAmgAlpha = 1.8;
+
+// ------------------------------------------------------ host: hierarchy --
+
+namespace {
+
+struct Graph {
+    int n = 0;
+    std::vector<int32_t> a, b;     // edges, a < b, ordered by (a, b)
+    std::vector<double> w;
+};
+
+bool prefer(double wc, int jc, double wb, int jb)
+{
+    if (jb < 0) return true;
+    if (wc > wb * (1.0 + kAmgTie)) return true;
+    return wc >= wb * (1.0 - kAmgTie) && jc < jb;
+}
+
+// One pairwise-matching pass; returns the number of aggregates.
+int match(const Graph &g, std::vector<int32_t> &assign)
+{
+    const size_t ne = g.a.size();
+    std::vector<int32_t> off(g.n + 1, 0);
+    for (size_t e = 0; e < ne; ++e) { ++off[g.a[e] + 1]; ++off[g.b[e] + 1]; }
+    for (int i = 0; i < g.n; ++i) off[i + 1] += off[i];
+    std::vector<int32_t> nb(2 * ne), cur(off.begin(), off.end() - 1);
+    std::vector<double> nw(2 * ne);
+    for (size_t e = 0; e < ne; ++e) {
+        nb[cur[g.a[e]]] = g.b[e]; nw[cur[g.a[e]]++] = g.w[e];
+        nb[cur[g.b[e]]] = g.a[e]; nw[cur[g.b[e]]++] = g.w[e];
+    }
+    assign.assign(g.n, -1);
+    int na = 0;
+    for (int i = 0; i < g.n; ++i) {
+        if (assign[i] >= 0) continue;
+        int best = -1, any = -1;
+        double wbest = 0.0, wany = 0.0;
+        for (int t = off[i]; t < off[i + 1]; ++t) {
+            const int j = nb[t];
+            if (assign[j] < 0 && prefer(nw[t], j, wbest, best)) { best = j; wbest = nw[t]; }
+            if (prefer(nw[t], j, wany, any)) { any = j; wany = nw[t]; }
+        }
+        if (best >= 0) assign[i] = assign[best] = na++;
+        else assign[i] = any >= 0 ? assign[any] : na++;
+    }
+    return na;
+}
+
+// Coarse graph of an assignment; emap: fine edge -> coarse edge or -1.
+Graph contract(const Graph &g, const std::vector<int32_t> &assign, int na,
+               std::vector<int32_t> &emap)
+{
+    const size_t ne = g.a.size();
+    emap.assign(ne, -1);
+    std::vector<std::pair<uint64_t, int32_t>> key;
+    key.reserve(ne);
+    for (size_t e = 0; e < ne; ++e) {
+        const uint32_t p = assign[g.a[e]], q = assign[g.b[e]];
+        if (p == q) continue;
+        const uint64_t lo = std::min(p, q), hi = std::max(p, q);
+        key.emplace_back((lo << 32) | hi, (int32_t)e);
+    }
+    std::sort(key.begin(), key.end());
+    Graph c;
+    c.n = na;
+    for (size_t t = 0; t < key.size(); ++t) {
+        if (t == 0 || key[t].first != key[t - 1].first) {
+            c.a.push_back((int32_t)(key[t].first >> 32));
+            c.b.push_back((int32_t)(key[t].first & 0xffffffffu));
+            c.w.push_back(0.0);
+        }
+        emap[key[t].second] = (int32_t)c.a.size() - 1;
+    }
+    for (size_t e = 0; e < ne; ++e)
+        if (emap[e] >= 0) c.w[emap[e]] += g.w[e];
+    return c;
+}
+
+// One level: two matching passes composed.
+Graph coarsen(const Graph &g, std::vector<int32_t> &agg, std::vector<int32_t> &emap)
+{
+    std::vector<int32_t> a1, a2, m1, m2;
+    const int n1 = match(g, a1);
+    const Graph g1 = contract(g, a1, n1, m1);
+    const int n2 = match(g1, a2);
+    Graph g2 = contract(g1, a2, n2, m2);
+    agg.resize(g.n);
+    for (int i = 0; i < g.n; ++i) agg[i] = a2[a1[i]];
+    emap.resize(g.a.size());
+    for (size_t e = 0; e < g.a.size(); ++e) emap[e] = m1[e] < 0 ? -1 : m2[m1[e]];
+    return g2;
+}
+
+}  // namespace
+
+// ---------------------------------------------------- device hierarchy --
+
+struct AmgLevelDev {
+    int n, ne;
+    const int32_t *rptr, *rcol, *redge;      // rows: off-diagonal entries, ascending column
+    const int32_t *agg;                      // -> next level (nullptr at the coarsest)
+    const int32_t *mptr, *memb;              // members in the finer level (l > 0)
+    const int32_t *iptr, *inner;             // finer-level edges inside the aggregate (l > 0)
+    const int32_t *eptr, *elist;             // finer-level edges of each edge (l > 0)
+    double *d, *o, *dinv;                    // matrix (level 0: d and o unused)
+    double *b, *x, *xa;                      // right-hand side, iterates
+};
+
+struct AmgData {
+    int L = 0;                // index of the coarsest level
+    int G = 1;                // levels 0..G-1 run over the whole grid
+    int grid = 0;             // cooperative grid size
+    int n[kAmgMaxLev] = {}, ne[kAmgMaxLev] = {};
+    AmgLevelDev *lev = nullptr;      // device copy of the level table
+    double *chol = nullptr;          // coarsest factor [nc * nc]
+    int *coarse_ok = nullptr;
+    double *z = nullptr, *p = nullptr, *q = nullptr, *r = nullptr;
+    DeviceArena arena;
+};
+
+void amg_release(AmgData *a)
+{
+    if (!a) return;
+    a->arena.release();
+    delete a;
+}
+
+namespace {
+
+struct AmgArgs {
+    int L, G, nc;
+    const AmgLevelDev *lev;
+    const double *d0, *o0;     // level-0 matrix: diagonal [N] and edge coefficients [F]
+    double o0_sign;            // o = o0_sign * o0[f] (-1 when o0 holds the positive a_f)
+    double *chol;
+    const double *b;
+    double *x, *r, *z, *p, *q;
+    double *partA, *partB;
+    int *coarse_ok;            // written by block 0 during setup, read after a barrier
+    GridBar *bar;
+    long long spin;
+    double tol, reltol;
+    int maxit;
+    DevSolveStats *stats;
+};
+
+struct AmgScal {
+    double alpha, beta, rho, thresh, nb, nr0, nr;
+    int phase;    // 0 iterate, 1 converged, 2 not converged, 3 breakdown, 4 zero rhs, 5 bad coarse
+};
+
+// Rows [lo, hi) of level l owned by this block (whole grid) or all rows
+// (block 0 alone).
+struct Span {
+    int lo, hi;
+};
+
+__device__ __forceinline__ Span grid_rows(int n)
+{
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int lo = min(n, (int)blockIdx.x * chunk);
+    return {lo, min(n, lo + chunk)};
+}
+
+__device__ __forceinline__ double coef(const AmgArgs &a, const AmgLevelDev &L, int l, int e)
+{
+    return l == 0 ? a.o0_sign * a.o0[e] : L.o[e];
+}
+
+__device__ __forceinline__ double diagv(const AmgArgs &a, const AmgLevelDev &L, int l, int i)
+{
+    return l == 0 ? a.d0[i] : L.d[i];
+}
+
+// (A x)_i on level l
+__device__ __forceinline__ double row_ax(const AmgArgs &a, const AmgLevelDev &L, int l, int i,
+                                         const double *x)
+{
+    double t = diagv(a, L, l, i) * x[i];
+    for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) t += coef(a, L, l, L.redge[e]) * x[L.rcol[e]];
+    return t;
+}
+
+// ---- level phases over the rows [s.lo, s.hi) with thread stride `step` --
+
+// Galerkin coarse matrix of level l (>= 1) from level l - 1.
+__device__ void phase_galerkin(const AmgArgs &a, int l, Span s, int t0, int step)
+{
+    const AmgLevelDev &C = a.lev[l], &F = a.lev[l - 1];
+    for (int I = s.lo + t0; I < s.hi; I += step) {
+        double v = 0.0;
+        for (int k = C.mptr[I]; k < C.mptr[I + 1]; ++k) v += diagv(a, F, l - 1, C.memb[k]);
+        for (int k = C.iptr[I]; k < C.iptr[I + 1]; ++k) v += 2.0 * coef(a, F, l - 1, C.inner[k]);
+        C.d[I] = v;
+        C.dinv[I] = 1.0 / v;
+    }
+}
+
+__device__ void phase_galerkin_edges(const AmgArgs &a, int l, Span s, int t0, int step)
+{
+    const AmgLevelDev &C = a.lev[l], &F = a.lev[l - 1];
+    for (int E = s.lo + t0; E < s.hi; E += step) {
+        double v = 0.0;
+        for (int k = C.eptr[E]; k < C.eptr[E + 1]; ++k) v += coef(a, F, l - 1, C.elist[k]);
+        C.o[E] = v;
+    }
+}
+
+// x = x + omega (b - A x) / d, from xin to xout
+__device__ void phase_sweep(const AmgArgs &a, int l, const double *xin, double *xout, Span s,
+                            int t0, int step)
+{
+    const AmgLevelDev &L = a.lev[l];
+    for (int i = s.lo + t0; i < s.hi; i += step)
+        xout[i] = xin[i] + kAmgOmega * (L.b[i] - row_ax(a, L, l, i, xin)) * L.dinv[i];
+}
+
+// b_{l+1} = P^T (b - A xa) over each aggregate, and the next level's first
+// sweep from zero: x_{l+1} = omega b_{l+1} / d_{l+1}.
+__device__ void phase_restrict(const AmgArgs &a, int l, Span s, int t0, int step)
+{
+    const AmgLevelDev &F = a.lev[l], &C = a.lev[l + 1];
+    for (int I = s.lo + t0; I < s.hi; I += step) {
+        double v = 0.0;
+        for (int k = C.mptr[I]; k < C.mptr[I + 1]; ++k) {
+            const int i = C.memb[k];
+            v += F.b[i] - row_ax(a, F, l, i, F.xa);
+        }
+        C.b[I] = v;
+        C.x[I] = kAmgOmega * v * C.dinv[I];
+    }
+}
+
+// x = xa + alpha P e_c, then one sweep; neighbours' prolonged values are
+// formed on the fly.
+__device__ void phase_prolong_sweep(const AmgArgs &a, int l, Span s, int t0, int step)
+{
+    const AmgLevelDev &L = a.lev[l];
+    const double *ec = a.lev[l + 1].xa;
+    for (int i = s.lo + t0; i < s.hi; i += step) {
+        const double xi = L.xa[i] + kAmgAlpha * ec[L.agg[i]];
+        double t = diagv(a, L, l, i) * xi;
+        for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) {
+            const int j = L.rcol[e];
+            t += coef(a, L, l, L.redge[e]) * (L.xa[j] + kAmgAlpha * ec[L.agg[j]]);
+        }
+        L.x[i] = xi + kAmgOmega * (L.b[i] - t) * L.dinv[i];
+    }
+}
+
+// Coarsest level: dense Cholesky factor (once per solve) by warp 0 of
+// block 0; returns false if the matrix is not positive definite.
+__device__ bool coarse_factor(const AmgArgs &a)
+{
+    const AmgLevelDev &C = a.lev[a.L];
+    const int n = a.nc, lane = threadIdx.x & 31;
+    double *c = a.chol;
+    for (int t = lane; t < n * n; t += 32) c[t] = 0.0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) c[i * n + i] = diagv(a, C, a.L, i);
+    for (int i = lane; i < n; i += 32)
+        for (int e = C.rptr[i]; e < C.rptr[i + 1]; ++e)
+            c[i * n + C.rcol[e]] = coef(a, C, a.L, C.redge[e]);
+    __syncwarp();
+    bool ok = true;
+    for (int j = 0; j < n; ++j) {
+        // left-looking column j: lanes own the rows i >= j
+        double s = c[j * n + j];
+        for (int k = 0; k < j; ++k) s -= c[j * n + k] * c[j * n + k];
+        if (!(s > 0.0)) ok = false;
+        const double ljj = sqrt(s > 0.0 ? s : 1.0);
+        for (int i = j + 1 + lane; i < n; i += 32) {
+            double t = c[i * n + j];
+            for (int k = 0; k < j; ++k) t -= c[i * n + k] * c[j * n + k];
+            c[i * n + j] = t / ljj;
+        }
+        __syncwarp();
+        if (lane == 0) c[j * n + j] = ljj;
+        __syncwarp();
+    }
+    return ok;
+}
+
+// xa_L = A_L^-1 b_L with the factor (warp 0 of block 0)
+__device__ void coarse_solve(const AmgArgs &a)
+{
+    const AmgLevelDev &C = a.lev[a.L];
+    const int n = a.nc, lane = threadIdx.x & 31;
+    const double *c = a.chol;
+    double *y = C.xa;
+    for (int i = lane; i < n; i += 32) y[i] = C.b[i];
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {            // forward: L y = b
+        const double yk = y[k] / c[k * n + k];
+        __syncwarp();
+        for (int i = k + 1 + lane; i < n; i += 32) y[i] -= c[i * n + k] * yk;
+        if (lane == 0) y[k] = yk;
+        __syncwarp();
+    }
+    for (int k = n - 1; k >= 0; --k) {       // backward: L^T x = y
+        const double xk = y[k] / c[k * n + k];
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) y[i] -= c[k * n + i] * xk;
+        if (lane == 0) y[k] = xk;
+        __syncwarp();
+    }
+}
+
+// The levels from G down to the coarsest and back, inside block 0.
+__device__ void block_levels_down_up(const AmgArgs &a)
+{
+    const int t0 = threadIdx.x, step = blockDim.x;
+    for (int l = a.G; l < a.L; ++l) {
+        const Span s{0, a.lev[l].n};
+        phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, s, t0, step);
+        __syncthreads();
+        phase_restrict(a, l, Span{0, a.lev[l + 1].n}, t0, step);
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) coarse_solve(a);
+    __syncthreads();
+    for (int l = a.L - 1; l >= a.G; --l) {
+        const Span s{0, a.lev[l].n};
+        phase_prolong_sweep(a, l, s, t0, step);
+        __syncthreads();
+        phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, s, t0, step);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
+{
+    __shared__ double buf[2][kAmgBlock];
+    __shared__ double tot[2];
+    __shared__ AmgScal sc;
+    __shared__ int s_coarse_ok;
+    const int t0 = threadIdx.x, step = blockDim.x;
+    const AmgLevelDev &L0 = a.lev[0];
+    const int N = L0.n;
+    const Span s0 = grid_rows(N);
+    unsigned gen = 0;
+    bool ok = true;
+    int it = 0;
+
+    // ---- setup: 1/diag on level 0, Galerkin matrices, coarsest factor
+    for (int i = s0.lo + t0; i < s0.hi; i += step) L0.dinv[i] = 1.0 / a.d0[i];
+    for (int l = 1; l < a.G && l <= a.L && ok; ++l) {
+        ok = grid_sync(a.bar, gen, a.spin);
+        if (!ok) break;
+        phase_galerkin(a, l, grid_rows(a.lev[l].n), t0, step);
+        phase_galerkin_edges(a, l, grid_rows(a.lev[l].ne), t0, step);
+    }
+    if (ok) ok = grid_sync(a.bar, gen, a.spin);
+    if (blockIdx.x == 0) {
+        for (int l = a.G; l <= a.L; ++l) {
+            if (l == 0) continue;
+            phase_galerkin(a, l, Span{0, a.lev[l].n}, t0, step);
+            phase_galerkin_edges(a, l, Span{0, a.lev[l].ne}, t0, step);
+            __syncthreads();
+        }
+        if (threadIdx.x < 32) {
+            const bool cok = coarse_factor(a);
+            if (threadIdx.x == 0) s_coarse_ok = cok ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *(volatile int *)a.coarse_ok = s_coarse_ok;
+    }
+
+    // ---- r = b - A x, norms
+    if (ok) {
+        double v[2] = {0.0, 0.0};
+        for (int i = s0.lo + t0; i < s0.hi; i += step) {
+            const double bi = a.b[i];
+            const double ri = bi - row_ax(a, L0, 0, i, a.x);
+            a.r[i] = ri;
+            L0.x[i] = kAmgOmega * ri * L0.dinv[i];      // first pre-smoothing sweep
+            v[0] += bi * bi;
+            v[1] += ri * ri;
+        }
+        ok = cg_grid_sum<2, kAmgBlock>(v, a.partB, a.bar, gen, a.spin, buf, tot);
+    }
+    if (threadIdx.x == 0) {
+        sc.nb = sqrt(tot[0]);
+        sc.nr0 = sqrt(tot[1]);
+        sc.nr = sc.nr0;
+        sc.thresh = fmax(a.tol * sc.nb, a.reltol * sc.nr0);
+        sc.alpha = sc.beta = sc.rho = 0.0;
+        sc.phase = sc.nb == 0.0 ? 4 : (sc.nr0 <= sc.thresh ? 1 : (a.maxit <= 0 ? 2 : 0));
+        if (ok && sc.phase == 0 && *(volatile int *)a.coarse_ok == 0) sc.phase = 5;
+    }
+    __syncthreads();
+    if (ok && sc.phase == 4) {
+        for (int i = s0.lo + t0; i < s0.hi; i += step) a.x[i] = 0.0;
+    } else if (ok && sc.phase == 0) {
+        while (true) {
+            // ---- z = V(r): level 0's b is r, its result lands in xa = z
+            for (int l = 0; l < a.G && l < a.L; ++l) {
+                // (the barrier before the first sweep of level 0 is the one
+                // that ended the previous phase)
+                if (l > 0 && !(ok = grid_sync(a.bar, gen, a.spin))) break;
+                phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, grid_rows(a.lev[l].n), t0, step);
+                if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+                phase_restrict(a, l, grid_rows(a.lev[l + 1].n), t0, step);
+            }
+            if (!ok) break;
+            if (a.L == 0) {
+                // a single level: the exact solve
+                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve(a);
+            } else {
+                if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+                if (blockIdx.x == 0) block_levels_down_up(a);
+            }
+            double v1[1] = {0.0};
+            for (int l = min(a.G, a.L) - 1; l >= 0; --l) {
+                if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+                phase_prolong_sweep(a, l, grid_rows(a.lev[l].n), t0, step);
+                if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+                phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, grid_rows(a.lev[l].n), t0, step);
+            }
+            if (!ok) break;
+            if (a.L == 0 && !(ok = grid_sync(a.bar, gen, a.spin))) break;
+            // rho = r.z (z = level 0's xa)
+            for (int i = s0.lo + t0; i < s0.hi; i += step) v1[0] += a.r[i] * L0.xa[i];
+            if (!(ok = cg_grid_sum<1, kAmgBlock>(v1, a.partA, a.bar, gen, a.spin, buf, tot))) break;
+            ++it;
+            if (threadIdx.x == 0) {
+                const double rho = tot[0];
+                sc.beta = it == 1 ? 0.0 : rho / sc.rho;
+                sc.rho = rho;
+                if (!(rho > 0.0) || !isfinite(rho)) sc.phase = 3;
+            }
+            __syncthreads();
+            if (sc.phase == 3) break;
+            // ---- p = z + beta p
+            const double beta = sc.beta;
+            for (int i = s0.lo + t0; i < s0.hi; i += step)
+                a.p[i] = it == 1 ? L0.xa[i] : L0.xa[i] + beta * a.p[i];
+            if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+            // ---- q = A p, p.q
+            double v2[1] = {0.0};
+            for (int i = s0.lo + t0; i < s0.hi; i += step) {
+                const double qi = row_ax(a, L0, 0, i, a.p);
+                a.q[i] = qi;
+                v2[0] += a.p[i] * qi;
+            }
+            if (!(ok = cg_grid_sum<1, kAmgBlock>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                const double pq = tot[0];
+                if (!(pq > 0.0) || !isfinite(pq)) { sc.phase = 3; sc.alpha = 0.0; }
+                else sc.alpha = sc.rho / pq;
+            }
+            __syncthreads();
+            if (sc.phase == 3) break;
+            // ---- x += alpha p, r -= alpha q, ||r||; next cycle's first sweep
+            const double alpha = sc.alpha;
+            double v3[1] = {0.0};
+            for (int i = s0.lo + t0; i < s0.hi; i += step) {
+                a.x[i] += alpha * a.p[i];
+                const double ri = a.r[i] - alpha * a.q[i];
+                a.r[i] = ri;
+                L0.x[i] = kAmgOmega * ri * L0.dinv[i];
+                v3[0] += ri * ri;
+            }
+            if (!(ok = cg_grid_sum<1, kAmgBlock>(v3, a.partA, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                sc.nr = sqrt(tot[0]);
+                if (!isfinite(sc.nr)) sc.phase = 3;
+                else if (sc.nr <= sc.thresh) sc.phase = 1;
+                else if (it >= a.maxit) sc.phase = 2;
+            }
+            __syncthreads();
+            if (sc.phase != 0) break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int ph = sc.phase;
+        a.stats->iters = it;
+        a.stats->status = !ok ? FV_E_TIMEOUT
+                        : (ph == 3 || ph == 5) ? FV_E_DIVERGED
+                        : ph == 2 ? FV_E_NOT_CONVERGED : FV_OK;
+        const bool zero = ph == 4;
+        a.stats->res0 = zero ? 0.0 : sc.nr0 / sc.nb;
+        a.stats->res = zero ? 0.0 : sc.nr / sc.nb;
+        a.stats->outer = 1;
+    }
+}
+
+// ------------------------------------------------------------ building --
+
+template <class T>
+fv_status upload(DeviceArena &ar, const T **d, const std::vector<T> &h)
+{
+    T *p = nullptr;
+    fv_status st = ar.alloc_n(&p, h.empty() ? 1 : h.size());
+    if (st != FV_OK) return st;
+    if (!h.empty() && cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FV_E_CUDA;
+    *d = p;
+    return FV_OK;
+}
+
+// rows of a graph: off-diagonal entries in ascending column (= ascending edge)
+void graph_rows(const Graph &g, std::vector<int32_t> &rptr, std::vector<int32_t> &rcol,
+                std::vector<int32_t> &redge)
+{
+    const size_t ne = g.a.size();
+    rptr.assign(g.n + 1, 0);
+    for (size_t e = 0; e < ne; ++e) { ++rptr[g.a[e] + 1]; ++rptr[g.b[e] + 1]; }
+    for (int i = 0; i < g.n; ++i) rptr[i + 1] += rptr[i];
+    rcol.resize(2 * ne);
+    redge.resize(2 * ne);
+    std::vector<int32_t> cur(rptr.begin(), rptr.end() - 1);
+    // edges are ordered by (a, b): for row i the edges with b == i (columns
+    // a < i) come in ascending a, then those with a == i in ascending b
+    for (size_t e = 0; e < ne; ++e) {
+        const int i = g.b[e];
+        rcol[cur[i]] = g.a[e]; redge[cur[i]++] = (int32_t)e;
+    }
+    for (size_t e = 0; e < ne; ++e) {
+        const int i = g.a[e];
+        rcol[cur[i]] = g.b[e]; redge[cur[i]++] = (int32_t)e;
+    }
+}
+
+// CSR of the items k (ascending) grouped by key[k] in [0, n); items with key < 0 skipped
+void group(int n, const std::vector<int32_t> &key, std::vector<int32_t> &ptr,
+           std::vector<int32_t> &list)
+{
+    ptr.assign(n + 1, 0);
+    for (int32_t k : key) if (k >= 0) ++ptr[k + 1];
+    for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+    list.resize(ptr[n]);
+    std::vector<int32_t> cur(ptr.begin(), ptr.end() - 1);
+    for (size_t t = 0; t < key.size(); ++t)
+        if (key[t] >= 0) list[cur[key[t]]++] = (int32_t)t;
+}
+
+fv_status amg_build(fv_mesh *m, AmgData **out)
+{
+    const int N = m->N, F = m->F;
+    // level-0 weights |S_f| Delta_f from the device geometry
+    std::vector<double> mag(F), del(F);
+    if (F > 0) {
+        FV_CUDA(cudaStreamSynchronize(m->stream));
+        FV_CUDA(cudaMemcpy(mag.data(), m->magSf, sizeof(double) * F, cudaMemcpyDeviceToHost));
+        FV_CUDA(cudaMemcpy(del.data(), m->delta, sizeof(double) * F, cudaMemcpyDeviceToHost));
+    }
+    std::vector<Graph> g(1);
+    g[0].n = N;
+    g[0].a.assign(m->plan.own.begin(), m->plan.own.begin() + F);
+    g[0].b.assign(m->plan.nei.begin(), m->plan.nei.begin() + F);
+    g[0].w.resize(F);
+    for (int f = 0; f < F; ++f) g[0].w[f] = mag[f] * del[f];
+    std::vector<std::vector<int32_t>> agg, emap;
+    while (g.back().n > kAmgNmin && (int)g.size() < kAmgMaxLev) {
+        std::vector<int32_t> ag, em;
+        Graph c = coarsen(g.back(), ag, em);
+        if ((double)c.n > 0.9 * g.back().n) break;
+        agg.push_back(std::move(ag));
+        emap.push_back(std::move(em));
+        g.push_back(std::move(c));
+    }
+    const int L = (int)g.size() - 1;
+    FV_CHECK(g[L].n <= kAmgCoarseMax, FV_E_UNSUPPORTED,
+             "multigrid coarsening stalled at %d nodes (the mesh graph is too weakly connected)",
+             g[L].n);
+    AmgData *h = new (std::nothrow) AmgData();
+    FV_CHECK(h != nullptr, FV_E_NOMEM, "host allocation failed");
+    h->L = L;
+    int G = 1;
+    while (G <= L && g[G].n > kAmgBlockRows) ++G;
+    h->G = G;
+    std::vector<AmgLevelDev> lv(L + 1);
+    DeviceArena &ar = h->arena;
+    fv_status st = FV_OK;
+    auto fail = [&](fv_status s) { amg_release(h); return s; };
+    for (int l = 0; l <= L; ++l) {
+        AmgLevelDev &d = lv[l];
+        std::memset(&d, 0, sizeof(d));
+        d.n = g[l].n;
+        d.ne = (int)g[l].a.size();
+        h->n[l] = d.n;
+        h->ne[l] = d.ne;
+        std::vector<int32_t> rptr, rcol, redge;
+        graph_rows(g[l], rptr, rcol, redge);
+        if ((st = upload(ar, &d.rptr, rptr)) != FV_OK) return fail(st);
+        if ((st = upload(ar, &d.rcol, rcol)) != FV_OK) return fail(st);
+        if ((st = upload(ar, &d.redge, redge)) != FV_OK) return fail(st);
+        if (l < L && (st = upload(ar, &d.agg, agg[l])) != FV_OK) return fail(st);
+        if (l > 0) {
+            std::vector<int32_t> ptr, list, inner_key(g[l - 1].a.size(), -1);
+            group(d.n, agg[l - 1], ptr, list);
+            if ((st = upload(ar, &d.mptr, ptr)) != FV_OK) return fail(st);
+            if ((st = upload(ar, &d.memb, list)) != FV_OK) return fail(st);
+            for (size_t e = 0; e < inner_key.size(); ++e)
+                if (emap[l - 1][e] < 0) inner_key[e] = agg[l - 1][g[l - 1].a[e]];
+            group(d.n, inner_key, ptr, list);
+            if ((st = upload(ar, &d.iptr, ptr)) != FV_OK) return fail(st);
+            if ((st = upload(ar, &d.inner, list)) != FV_OK) return fail(st);
+            group(d.ne, emap[l - 1], ptr, list);
+            if ((st = upload(ar, &d.eptr, ptr)) != FV_OK) return fail(st);
+            if ((st = upload(ar, &d.elist, list)) != FV_OK) return fail(st);
+            if ((st = ar.alloc_n(&d.d, d.n)) != FV_OK) return fail(st);
+            if ((st = ar.alloc_n(&d.o, d.ne ? d.ne : 1)) != FV_OK) return fail(st);
+        }
+        if ((st = ar.alloc_n(&d.dinv, d.n)) != FV_OK) return fail(st);
+        if (l > 0 && (st = ar.alloc_n(&d.b, d.n)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.x, d.n)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.xa, d.n)) != FV_OK) return fail(st);
+    }
+    if ((st = ar.alloc_n(&h->r, N)) != FV_OK) return fail(st);
+    if ((st = ar.alloc_n(&h->p, N)) != FV_OK) return fail(st);
+    if ((st = ar.alloc_n(&h->q, N)) != FV_OK) return fail(st);
+    lv[0].b = h->r;            // level 0 smooths the CG residual
+    h->z = lv[0].xa;
+    if ((st = ar.alloc_n(&h->chol, (size_t)g[L].n * g[L].n)) != FV_OK) return fail(st);
+    if ((st = ar.alloc_n(&h->coarse_ok, 1)) != FV_OK) return fail(st);
+    if ((st = ar.alloc_n(&h->lev, L + 1)) != FV_OK) return fail(st);
+    FV_CUDA(cudaMemcpy(h->lev, lv.data(), sizeof(AmgLevelDev) * (L + 1), cudaMemcpyHostToDevice));
+    int per_sm = 0;
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_amg, kAmgBlock, 0));
+    FV_CHECK(per_sm >= 1, FV_E_CUDA, "multigrid CG kernel cannot be resident");
+    h->grid = m->sm_count * std::min(per_sm, 2);
+    *out = h;
+    return FV_OK;
+}
+
+}  // namespace
+
+fv_status amg_prepare(fv_mesh *m)
+{
+    if (m->amg) return FV_OK;
+    AmgData *h = nullptr;
+    fv_status st = amg_build(m, &h);
+    if (st != FV_OK) return st;
+    m->amg = h;
+    return FV_OK;
+}
+
+fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
+{
+    fv_status st = amg_prepare(const_cast<fv_mesh *>(m));
+    if (st != FV_OK) return st;
+    const AmgData *h = m->amg;
+    const KrylovWork &w = m->kw;
+    AmgArgs a;
+    a.L = h->L;
+    a.G = h->G;
+    a.nc = h->n[h->L];
+    a.lev = h->lev;
+    a.d0 = pb.diag;
+    a.o0 = pb.off;
+    a.o0_sign = pb.off_sign;
+    a.chol = h->chol;
+    a.b = pb.b;
+    a.x = pb.x;
+    a.r = h->r;
+    a.z = h->z;
+    a.p = h->p;
+    a.q = h->q;
+    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
+    a.partA = w.partials;
+    a.partB = w.partials + (size_t)gp * kParts;
+    a.coarse_ok = h->coarse_ok;
+    a.bar = w.bar;
+    a.spin = g_spin_limit;
+    a.tol = pb.tol;
+    a.reltol = pb.reltol;
+    a.maxit = pb.maxit;
+    a.stats = pb.stats;
+    FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
+    // about 4 rows per thread before another block is worth a grid barrier
+    int G = (m->N + 4 * kAmgBlock - 1) / (4 * kAmgBlock);
+    G = std::max(1, std::min(std::min(G, h->grid), gp));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kAmgBlock);
+    cfg.stream = m->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {&a};
+    FV_CUDA(cudaLaunchKernelExC(&cfg, (const void *)k_pcg_amg, args));
+    return FV_OK;
+}
+
+}  // namespace fvgb
+
+using namespace fvgb;
+
+extern "C" fv_status fv_amg_coarsen_host(int32_t n, int32_t ne, const int32_t *ea,
+                                         const int32_t *eb, const double *ew, int32_t *agg,
+                                         int32_t *emap, int32_t *n_coarse, int32_t *ne_coarse,
+                                         int32_t *cea, int32_t *ceb, double *cew)
+{
+    FV_CHECK(n >= 0 && ne >= 0 && agg && n_coarse && ne_coarse, FV_E_INVALID, "bad arguments");
+    FV_CHECK(ne == 0 || (ea && eb && ew && emap && cea && ceb && cew), FV_E_INVALID,
+             "edge arrays missing");
+    Graph g;
+    g.n = n;
+    g.a.assign(ea, ea + ne);
+    g.b.assign(eb, eb + ne);
+    g.w.assign(ew, ew + ne);
+    for (int e = 0; e < ne; ++e) {
+        FV_CHECK(g.a[e] >= 0 && g.a[e] < g.b[e] && g.b[e] < n, FV_E_INVALID,
+                 "edge %d is not (lower, higher) within range", e);
+        FV_CHECK(e == 0 || g.a[e - 1] < g.a[e] || (g.a[e - 1] == g.a[e] && g.b[e - 1] < g.b[e]),
+                 FV_E_INVALID, "edges are not ordered by (lower, higher)");
+        FV_CHECK(g.w[e] > 0.0, FV_E_INVALID, "edge %d has a non-positive weight", e);
+    }
+    std::vector<int32_t> ag, em;
+    Graph c = coarsen(g, ag, em);
+    std::copy(ag.begin(), ag.end(), agg);
+    std::copy(em.begin(), em.end(), emap);
+    *n_coarse = c.n;
+    *ne_coarse = (int32_t)c.a.size();
+    std::copy(c.a.begin(), c.a.end(), cea);
+    std::copy(c.b.begin(), c.b.end(), ceb);
+    std::copy(c.w.begin(), c.w.end(), cew);
+    return FV_OK;
+}
+
+extern "C" fv_status fv_amg_info(const fv_mesh *mc, int32_t *n_levels, int32_t *sizes)
+{
+    FV_CHECK(mc && n_levels, FV_E_INVALID, "NULL argument");
+    fv_mesh *m = const_cast<fv_mesh *>(mc);
+    fv_status st = amg_prepare(m);
+    if (st != FV_OK) return st;
+    *n_levels = m->amg->L + 1;
+    if (sizes)
+        for (int l = 0; l <= m->amg->L; ++l) sizes[l] = m->amg->n[l];
+    return FV_OK;
+}

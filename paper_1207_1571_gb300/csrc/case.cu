@@ -65,6 +65,11 @@ void fill_solve(fv_solve_stats *o, const DevSolveStats &d)
 fv_status launch_pressure_solve(const fv_case *c, double tol, double reltol, int maxit,
                                 DevSolveStats *st)
 {
+    if (c->psolver == FV_PSOLVER_AMG) {
+        // the face coefficients a_f of the pressure assembly are -upper
+        AmgProblem ap{c->Pd, c->af, -1.0, c->pbv, c->p, tol, reltol, maxit, st};
+        return launch_pcg_amg(c->mesh, ap);
+    }
     if (c->precision == FV_PREC_MIXED) {
         MixedProblem mp{c->Pd, c->Po, c->pbv, c->p, tol, reltol, maxit, st};
         return launch_pcg_mixed(c->mesh, mp);
@@ -477,6 +482,44 @@ extern "C" fv_status fv_pcg_solve(const fv_mesh *mc, const double *diag, const d
     FV_CUDA(cudaStreamSynchronize(m->stream));
     if (stats) fill_solve(stats, h);
     return (fv_status)h.status;
+}
+
+extern "C" fv_status fv_pcg_solve_amg(const fv_mesh *mc, const double *diag, const double *upper,
+                                      const double *b, double *x, const fv_pcg_params *prm,
+                                      fv_solve_stats *stats)
+{
+    FV_CHECK(mc && diag && b && x && prm, FV_E_INVALID, "NULL argument");
+    FV_CHECK(mc->F == 0 || upper, FV_E_INVALID, "upper is NULL");
+    FV_CHECK(prm->maxit >= 0 && prm->tol >= 0.0 && prm->reltol >= 0.0, FV_E_INVALID, "bad params");
+    fv_mesh *m = const_cast<fv_mesh *>(mc);
+    fv_status st = amg_prepare(m);
+    if (st != FV_OK) return st;
+    AmgProblem ap{diag, upper, 1.0, b, x, prm->tol, prm->reltol, prm->maxit, m->kw.stats};
+    if ((st = launch_pcg_amg(m, ap)) != FV_OK) return st;
+    DevSolveStats h;
+    FV_CUDA(cudaMemcpyAsync(&h, m->kw.stats, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
+    FV_CUDA(cudaStreamSynchronize(m->stream));
+    if (stats) fill_solve(stats, h);
+    return (fv_status)h.status;
+}
+
+extern "C" fv_status fv_case_set_pressure_solver(fv_case *c, int32_t solver)
+{
+    FV_CHECK(c, FV_E_INVALID, "NULL case");
+    FV_CHECK(solver == FV_PSOLVER_JACOBI || solver == FV_PSOLVER_AMG, FV_E_INVALID,
+             "unknown pressure solver %d", solver);
+    FV_CHECK(solver == FV_PSOLVER_JACOBI || c->precision == FV_PREC_FP64, FV_E_UNSUPPORTED,
+             "the multigrid pressure solver runs in FP64 only");
+    if (solver == FV_PSOLVER_AMG) {
+        fv_status st = amg_prepare(const_cast<fv_mesh *>(c->mesh));
+        if (st != FV_OK) return st;
+    }
+    if (c->psolver != solver && c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->psolver = solver;
+    return FV_OK;
 }
 
 extern "C" fv_status fv_pcg_solve_mixed(const fv_mesh *mc, const double *diag, const double *upper,

@@ -103,6 +103,20 @@ struct KrylovWork {
     DevSolveStats *stats = nullptr;  // [4] scratch for stand-alone calls
 };
 
+// aggregation-multigrid preconditioned CG (amg.cu)
+struct AmgData;
+void amg_release(AmgData *a);
+struct AmgProblem {
+    const double *diag;      // [N]
+    const double *off;       // [F] symmetric off-diagonal per internal face, times off_sign
+    double off_sign;
+    const double *b;         // [N]
+    double *x;               // [N] in/out
+    double tol, reltol;
+    int maxit;
+    DevSolveStats *stats;    // device
+};
+
 }  // namespace fvgb
 
 struct fv_mesh {
@@ -125,12 +139,19 @@ struct fv_mesh {
     double *Sf = nullptr, *magSf = nullptr, *w = nullptr, *delta = nullptr, *kv = nullptr;
     double *V = nullptr, *Vinv = nullptr;
     fvgb::KrylovWork kw;
+    fvgb::AmgData *amg = nullptr;     // multigrid hierarchy, built on first use
 };
+
+namespace fvgb {
+fv_status amg_prepare(fv_mesh *m);
+fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb);
+}
 
 struct fv_case {
     const fv_mesh *mesh = nullptr;
     double nu = 0.0;
     int precision = FV_PREC_FP64;
+    int psolver = FV_PSOLVER_JACOBI;
     fvgb::DeviceArena arena;
     // state
     double *u = nullptr, *p = nullptr, *phi = nullptr;   // [3N], [N], [M]

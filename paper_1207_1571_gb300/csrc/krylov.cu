@@ -24,12 +24,12 @@
 #include <cooperative_groups.h>
 
 #include "fvgb_internal.h"
+#include "coop.cuh"
 
 namespace fvgb {
 
 long long g_spin_limit = 1LL << 25;
 constexpr int kBlock = 512;
-constexpr int kParts = 8;       // doubles per block per partial record
 
 struct RowSpan {
     int e0, K;
@@ -43,49 +43,7 @@ __device__ __forceinline__ RowSpan row_span(const int32_t *__restrict__ slice_pt
 }
 
 // ------------------------------------------------------------ barriers --
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Returns false (for every thread of the block) when the barrier gave up or
-// another block recorded an error.
-__device__ bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (gridDim.x == 1) return true;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicExch(&bar->gen, g + 1);
-        } else {
-            long long spins = 0;
-            while (ld_acquire(&bar->gen) == g) {
-                if (++spins > limit) {
-                    atomicExch(&bar->err, FV_E_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 256) __nanosleep(32);
-            }
-        }
-        __threadfence();
-        if (*(volatile int *)&bar->err != 0) ok = 0;
-        s_ok = ok;
-    }
-    ++gen;
-    __syncthreads();
-    return s_ok != 0;
-}
+// (grid barrier and deterministic reductions: coop.cuh)
 
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV])
@@ -145,85 +103,8 @@ __device__ bool grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &
 // [b*chunk, (b+1)*chunk) (whole 32-row slices) for the whole solve, so the
 // neighbour gathers of a block mostly hit its own SM's L1.  Gathers are
 // plain loads: the grid barrier's acquire orders them after the writes of
-// the previous phase.
-//
-// Reductions keep FP64 work low (GB300 runs FP64 at about 2 FMA per clock
-// per SM): threads drop their partial sums into shared memory and one warp
-// adds them in a fixed order; after the grid barrier one warp adds the
-// per-block partials, again in a fixed order.
-
-constexpr int kCgBlock = 1024;
-constexpr int kRedWarps = 4;        // one reducing warp per SM sub-partition
-
-__device__ __forceinline__ double warp_sum(double x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// Block sum of NV values.  Threads store their partials in shared memory;
-// warps 0..3 (one per SM sub-partition, so their FP64 work runs in
-// parallel) each add a quarter of them, then thread 0 adds the four results.
-// The order of every addition is fixed.  On return tot[k] (shared) holds the
-// sums; only thread 0 is guaranteed to have seen them before the trailing
-// __syncthreads of the caller.
-template <int NV>
-__device__ __forceinline__ void cg_block_sum(const double (&v)[NV], double (*buf)[kCgBlock],
-                                             double *tot)
-{
-    __shared__ double quarter[NV][kRedWarps];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < kRedWarps) {
-        constexpr int per = kCgBlock / kRedWarps;      // values per warp
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
-#pragma unroll
-            for (int j = 0; j < per / 32; ++j) x += buf[k][w * per + lane + 32 * j];
-            x = warp_sum(x);
-            if (lane == 0) quarter[k][w] = x;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
-#pragma unroll
-            for (int q = 0; q < kRedWarps; ++q) x += quarter[k][q];
-            tot[k] = x;
-        }
-    }
-}
-
-// Grid sum of NV values; on return thread 0 of every block holds the same
-// bits in tot[] (shared).  Returns false (all threads) if the barrier failed.
-template <int NV>
-__device__ bool cg_grid_sum(const double (&v)[NV], double *part, GridBar *bar, unsigned &gen,
-                            long long limit, double (*buf)[kCgBlock], double *tot)
-{
-    cg_block_sum<NV>(v, buf, tot);
-    if (gridDim.x == 1) return true;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) part[blockIdx.x * kParts + k] = tot[k];
-    }
-    if (!grid_sync(bar, gen, limit)) return false;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < NV) {
-        // warp k adds quantity k over the blocks
-        double x = 0.0;
-        for (int j = lane; j < (int)gridDim.x; j += 32) x += __ldcg(part + j * kParts + w);
-        x = warp_sum(x);
-        if (lane == 0) tot[w] = x;
-    }
-    __syncthreads();
-    return true;
-}
+// the previous phase.  Reductions run over four warps, one per SM
+// sub-partition (coop.cuh).
 
 struct CgArgs {
     int N;

@@ -260,6 +260,8 @@ extern "C" fv_status fv_mesh_destroy(fv_mesh *m)
 {
     if (!m) return FV_OK;
     cudaStreamSynchronize(m->stream);
+    fvgb::amg_release(m->amg);
+    m->amg = nullptr;
     m->arena.release();
     delete m;
     return FV_OK;

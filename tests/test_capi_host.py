@@ -177,3 +177,39 @@ def test_ellj_builder_rejects_bad_patterns(P):
         P.ellj_build_host(np.array([0, 2, 3]), np.array([1, 0, 1]), 2)   # unsorted row
     with pytest.raises(P.FvError):
         P.ellj_build_host(np.array([0, 1]), np.array([0]), 0)            # K = 0
+
+
+# ------------------------------------------ multigrid hierarchy (host side) --
+
+@pytest.mark.parametrize("name", ["cube_perm", "tets", "cavity2d", "duct"])
+def test_amg_coarsening_matches_oracle(P, name):
+    """The library's coarsening, applied level by level to the level-0 graph
+    weighted by |S_f| Delta_f (the oracle's geometry, which the device
+    geometry reproduces bit for bit), gives the oracle's aggregates, edge
+    maps and coarse graphs exactly."""
+    m = MESHES[name]()
+    om = O.Mesh(m, renumber=True)
+    geo = om.geometry()
+    own, nei = om.addressing()
+    F = m.n_internal_faces
+    a, b, w = own[:F], nei, geo["magSf"][:F] * geo["delta"][:F]
+    amg = O.Amg(om)
+    n, ne = amg.levels()
+    cur_n = m.n_cells
+    for l in range(len(n) - 1):
+        lvl = P.amg_coarsen_host(cur_n, a, b, w)
+        agg, emap = amg.maps(l)
+        assert np.array_equal(lvl["agg"], agg) and np.array_equal(lvl["emap"], emap)
+        ea, eb = amg.edges(l + 1)
+        assert lvl["n"] == n[l + 1]
+        assert np.array_equal(lvl["a"], ea) and np.array_equal(lvl["b"], eb)
+        a, b, w, cur_n = lvl["a"], lvl["b"], lvl["w"], lvl["n"]
+
+
+def test_amg_coarsening_rejects_bad_graphs(P):
+    with pytest.raises(P.FvError):
+        P.amg_coarsen_host(3, [1], [0], [1.0])          # not (lower, higher)
+    with pytest.raises(P.FvError):
+        P.amg_coarsen_host(3, [0, 0], [2, 1], [1.0, 1.0])  # not ordered
+    with pytest.raises(P.FvError):
+        P.amg_coarsen_host(3, [0], [1], [0.0])          # weight not positive
