@@ -29,6 +29,7 @@
 // residual into the restriction, and the prolongation into the first
 // post-smoothing sweep, so a grid level costs four grid barriers per cycle.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -42,7 +43,7 @@ constexpr int kAmgMaxLev = 24;
 constexpr int kAmgNmin = 32;           // coarsest level size target
 constexpr int kAmgCoarseMax = 64;      // largest coarsest level handled on the device
 constexpr int kAmgBlock = 512;
-constexpr int kAmgBlockRows = 8192;    // levels up to this size run inside block 0
+constexpr int kAmgBlockRows = 1024;    // levels up to this size run inside block 0
 constexpr double kAmgTie = 1e-9;
 constexpr double kAmgOmega = 2.0 / 3.0;
 constexpr double kAmgAlpha = 1.8;
@@ -146,6 +147,7 @@ Graph coarsen(const Graph &g, std::vector<int32_t> &agg, std::vector<int32_t> &e
 struct AmgLevelDev {
     int n, ne;
     const int32_t *rptr, *rcol, *redge;      // rows: off-diagonal entries, ascending column
+    double *rv;                              // coefficient of every row entry (set per solve)
     const int32_t *agg;                      // -> next level (nullptr at the coarsest)
     const int32_t *mptr, *memb;              // members in the finer level (l > 0)
     const int32_t *iptr, *inner;             // finer-level edges inside the aggregate (l > 0)
@@ -220,13 +222,22 @@ __device__ __forceinline__ double diagv(const AmgArgs &a, const AmgLevelDev &L, 
     return l == 0 ? a.d0[i] : L.d[i];
 }
 
-// (A x)_i on level l
+// (A x)_i on level l (coefficients from the per-entry copy: no edge indirection)
 __device__ __forceinline__ double row_ax(const AmgArgs &a, const AmgLevelDev &L, int l, int i,
                                          const double *x)
 {
     double t = diagv(a, L, l, i) * x[i];
-    for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) t += coef(a, L, l, L.redge[e]) * x[L.rcol[e]];
+    const int e1 = L.rptr[i + 1];
+    for (int e = L.rptr[i]; e < e1; ++e) t += L.rv[e] * x[L.rcol[e]];
     return t;
+}
+
+// level 0's per-entry coefficients from the caller's edge array
+__device__ void phase_rows0(const AmgArgs &a, Span s, int t0, int step)
+{
+    const AmgLevelDev &L = a.lev[0];
+    for (int i = s.lo + t0; i < s.hi; i += step)
+        for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) L.rv[e] = coef(a, L, 0, L.redge[e]);
 }
 
 // ---- level phases over the rows [s.lo, s.hi) with thread stride `step` --
@@ -241,6 +252,13 @@ __device__ void phase_galerkin(const AmgArgs &a, int l, Span s, int t0, int step
         for (int k = C.iptr[I]; k < C.iptr[I + 1]; ++k) v += 2.0 * coef(a, F, l - 1, C.inner[k]);
         C.d[I] = v;
         C.dinv[I] = 1.0 / v;
+        // the row's coefficients: the same sums as the edge phase below
+        for (int e = C.rptr[I]; e < C.rptr[I + 1]; ++e) {
+            const int E = C.redge[e];
+            double w = 0.0;
+            for (int k = C.eptr[E]; k < C.eptr[E + 1]; ++k) w += coef(a, F, l - 1, C.elist[k]);
+            C.rv[e] = w;
+        }
     }
 }
 
@@ -290,7 +308,7 @@ __device__ void phase_prolong_sweep(const AmgArgs &a, int l, Span s, int t0, int
         double t = diagv(a, L, l, i) * xi;
         for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) {
             const int j = L.rcol[e];
-            t += coef(a, L, l, L.redge[e]) * (L.xa[j] + kAmgAlpha * ec[L.agg[j]]);
+            t += L.rv[e] * (L.xa[j] + kAmgAlpha * ec[L.agg[j]]);
         }
         L.x[i] = xi + kAmgOmega * (L.b[i] - t) * L.dinv[i];
     }
@@ -308,7 +326,7 @@ __device__ bool coarse_factor(const AmgArgs &a)
     for (int i = lane; i < n; i += 32) c[i * n + i] = diagv(a, C, a.L, i);
     for (int i = lane; i < n; i += 32)
         for (int e = C.rptr[i]; e < C.rptr[i + 1]; ++e)
-            c[i * n + C.rcol[e]] = coef(a, C, a.L, C.redge[e]);
+            c[i * n + C.rcol[e]] = C.rv[e];
     __syncwarp();
     bool ok = true;
     for (int j = 0; j < n; ++j) {
@@ -390,8 +408,10 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
     bool ok = true;
     int it = 0;
 
-    // ---- setup: 1/diag on level 0, Galerkin matrices, coarsest factor
+    // ---- setup: 1/diag and row coefficients on level 0, Galerkin matrices,
+    // coarsest factor
     for (int i = s0.lo + t0; i < s0.hi; i += step) L0.dinv[i] = 1.0 / a.d0[i];
+    phase_rows0(a, s0, t0, step);
     for (int l = 1; l < a.G && l <= a.L && ok; ++l) {
         ok = grid_sync(a.bar, gen, a.spin);
         if (!ok) break;
@@ -615,8 +635,12 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
     AmgData *h = new (std::nothrow) AmgData();
     FV_CHECK(h != nullptr, FV_E_NOMEM, "host allocation failed");
     h->L = L;
+    // levels above this size run over the whole grid (FVGB_AMG_BLOCK_ROWS
+    // overrides the default for tuning)
+    long block_rows = kAmgBlockRows;
+    if (const char *env = std::getenv("FVGB_AMG_BLOCK_ROWS")) block_rows = std::atol(env);
     int G = 1;
-    while (G <= L && g[G].n > kAmgBlockRows) ++G;
+    while (G < L && g[G].n > block_rows) ++G;
     h->G = G;
     std::vector<AmgLevelDev> lv(L + 1);
     DeviceArena &ar = h->arena;
@@ -634,6 +658,7 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
         if ((st = upload(ar, &d.rptr, rptr)) != FV_OK) return fail(st);
         if ((st = upload(ar, &d.rcol, rcol)) != FV_OK) return fail(st);
         if ((st = upload(ar, &d.redge, redge)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.rv, rcol.empty() ? 1 : rcol.size())) != FV_OK) return fail(st);
         if (l < L && (st = upload(ar, &d.agg, agg[l])) != FV_OK) return fail(st);
         if (l > 0) {
             std::vector<int32_t> ptr, list, inner_key(g[l - 1].a.size(), -1);

@@ -20,8 +20,34 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
-// Returns false (for every thread of the block) when the barrier gave up or
-// another block recorded an error.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier.  The block's writes are ordered before its arrival by the
+// block barrier and the release half of the arrival's atomic; the arrival
+// counter only grows within a launch (the host zeroes it before each), so
+// the last of the gridDim.x arrivals of generation g reads
+// (g + 1) * gridDim.x - 1 and publishes g + 1 with a release store, which
+// the waiters' acquire loads (then the block barrier) order before their
+// later reads.  A waiter gives up after `limit` polls and records
+// FV_E_TIMEOUT; waiters also leave when another block has recorded an
+// error.  Returns false (for every thread of the block) in both cases.
 __device__ inline bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
 {
     __shared__ int s_ok;
@@ -30,25 +56,25 @@ __device__ inline bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned g = gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicExch(&bar->gen, g + 1);
+        const unsigned old = atom_add_acq_rel(&bar->count, 1u);
+        if (old == (g + 1) * gridDim.x - 1) {
+            st_release(&bar->gen, g + 1);
         } else {
             long long spins = 0;
             while (ld_acquire(&bar->gen) == g) {
-                if (++spins > limit) {
+                ++spins;
+                if (spins > limit) {
                     atomicExch(&bar->err, FV_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if ((spins & 63) == 0 && ld_relaxed(&bar->err) != 0) {
                     ok = 0;
                     break;
                 }
                 if (spins > 256) __nanosleep(32);
             }
         }
-        __threadfence();
-        if (*(volatile int *)&bar->err != 0) ok = 0;
         s_ok = ok;
     }
     ++gen;
