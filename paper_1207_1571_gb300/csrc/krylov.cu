@@ -124,9 +124,41 @@ struct CgArgs {
 // only (one FP64 divide or square root costs a warp dozens of cycles per
 // instruction on this part, so no thread repeats it).
 struct CgScalars {
-    double alpha, beta, rho, thresh, nb, nr0, nr;
+    double alpha, beta, rho, thresh, nb, nr0, nr, dmin;
     int phase;       // 0 iterate, 1 converged, 2 not converged, 3 diverged, 4 zero rhs
+    int exact;       // evaluate ||D^1/2 r^|| in this iteration's residual update
 };
+
+// The stopping test needs ||r||_2 = ||D^1/2 r^||_2, two more FP64 operations
+// per row than the r^.r^ the iteration needs anyway.  Since ||D^1/2 r^||^2 >=
+// min(D) r^.r^, that norm is only evaluated once min(D) r^.r^ has come within
+// kNearStop of thresh^2 (or at the iteration limit); if r^.r^ then falls past
+// the bound in a single step, one extra pass evaluates it before the test.
+// A skipped evaluation could not have met the test (the bound holds with a
+// 1e-8 relative margin, far above the rounding of the sums), so iterates,
+// counts and results are those of evaluating it every iteration.
+constexpr double kNearStop = 16.0;
+constexpr double kBoundMargin = 1.0 + 1e-8;
+
+// Minimum over the block (all threads receive it).
+__device__ __forceinline__ double block_min(double v)
+{
+    __shared__ double wmin[kCgBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (int)(blockDim.x >> 5) ? wmin[threadIdx.x] : INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (threadIdx.x == 0) wmin[0] = w;
+    }
+    __syncthreads();
+    const double r = wmin[0];
+    __syncthreads();
+    return r;
+}
 
 // q = A^ p for one row of the unit-diagonal scaled matrix; all loads of
 // the row are issued before the first product (rows have <= 6 entries on
@@ -170,12 +202,19 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
     bool ok = true;
     int it = 0;
 
-    // S1: scaling s = D^-1/2 and scaled start y = D^1/2 x
-    for (int i = i0; i < re; i += kCgBlock) {
-        const double d = a.diag[i];
-        const double sq = sqrt(d);
-        a.s[i] = 1.0 / sq;
-        a.y[i] = a.x[i] * sq;
+    // S1: scaling s = D^-1/2 and scaled start y = D^1/2 x; the block's
+    // smallest diagonal (0 if any is not positive) in its partial record
+    {
+        double dmin = INFINITY;
+        for (int i = i0; i < re; i += kCgBlock) {
+            const double d = a.diag[i];
+            const double sq = sqrt(d);
+            a.s[i] = 1.0 / sq;
+            a.y[i] = a.x[i] * sq;
+            dmin = d > 0.0 ? fmin(dmin, d) : 0.0;
+        }
+        dmin = block_min(dmin);
+        if (threadIdx.x == 0) a.partA[blockIdx.x * kParts + kParts - 1] = dmin;
     }
     ok = grid_sync(a.bar, gen, a.spin);
     // S2: scale the off-diagonals, r^ = s (b - A x), norms
@@ -201,6 +240,16 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
         }
         ok = cg_grid_sum<3>(v3, a.partB, a.bar, gen, a.spin, buf, tot);
     }
+    if (threadIdx.x < 32) {
+        // smallest diagonal over the grid (written before the last barrier)
+        double m = INFINITY;
+        for (int j = threadIdx.x; j < (int)gridDim.x; j += 32)
+            m = fmin(m, __ldcg(a.partA + j * kParts + kParts - 1));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) sc.dmin = m;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         sc.nb = sqrt(tot[0]);
         sc.nr0 = sqrt(tot[1]);
@@ -209,6 +258,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
         sc.thresh = fmax(a.tol * sc.nb, a.reltol * sc.nr0);
         sc.alpha = sc.beta = 0.0;
         sc.phase = sc.nb == 0.0 ? 4 : (sc.nr0 <= sc.thresh ? 1 : 0);
+        sc.exact = 1;
     }
     __syncthreads();
     if (ok && sc.phase == 4) {
@@ -247,26 +297,44 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             }
             __syncthreads();
             if (sc.phase == 3) break;
-            // P3: r^ -= alpha q; r^.r^ and ||D^1/2 r^||^2
+            // P3: r^ -= alpha q; r^.r^, and ||D^1/2 r^||^2 near the stop
             const double alpha = sc.alpha;
+            const bool exact = sc.exact || it >= a.maxit;
             double v2[2] = {0.0, 0.0};
 #pragma unroll 2
             for (int i = i0; i < re; i += kCgBlock) {
                 const double ri = a.r[i] - alpha * a.q[i];
                 a.r[i] = ri;
-                const double r2 = ri * ri;
-                v2[0] += r2;
-                v2[1] += a.diag[i] * r2;
+                v2[0] += ri * ri;
+                if (exact) v2[1] += (a.diag[i] * ri) * ri;
             }
             if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
             if (threadIdx.x == 0) {
-                sc.nr = sqrt(tot[1]);
-                if (!isfinite(sc.nr)) sc.phase = 3;
-                else if (sc.nr <= sc.thresh) sc.phase = 1;
+                const double rho = tot[0];
+                const double t2 = sc.thresh * sc.thresh;
+                // an evaluation skipped while the bound still allows the stop
+                sc.exact = exact ? 1 : (sc.dmin * rho > t2 * kBoundMargin ? 0 : 2);
+            }
+            __syncthreads();
+            if (sc.exact == 2) {
+                double v4[1] = {0.0};
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const double ri = a.r[i];
+                    v4[0] += (a.diag[i] * ri) * ri;
+                }
+                if (!(ok = cg_grid_sum<1>(v4, a.partA, a.bar, gen, a.spin, buf, tot + 1))) break;
+            }
+            if (threadIdx.x == 0) {
+                const double rho = tot[0];
+                const bool have = sc.exact != 0;
+                sc.nr = have ? sqrt(tot[1]) : sqrt(sc.dmin * rho);   // a lower bound when skipped
+                if (!isfinite(sc.nr) || !isfinite(rho)) sc.phase = 3;
+                else if (have && sc.nr <= sc.thresh) sc.phase = 1;
                 else if (it >= a.maxit) sc.phase = 2;
                 else {
-                    sc.beta = tot[0] / sc.rho;
-                    sc.rho = tot[0];
+                    sc.beta = rho / sc.rho;
+                    sc.rho = rho;
+                    sc.exact = sc.dmin * rho <= kNearStop * sc.thresh * sc.thresh ? 1 : 0;
                 }
             }
             __syncthreads();
