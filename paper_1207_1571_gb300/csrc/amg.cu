@@ -146,8 +146,10 @@ Graph coarsen(const Graph &g, std::vector<int32_t> &agg, std::vector<int32_t> &e
 
 struct AmgLevelDev {
     int n, ne;
-    const int32_t *rptr, *rcol, *redge;      // rows: off-diagonal entries, ascending column
-    double *rv;                              // coefficient of every row entry (set per solve)
+    // rows in SELL-32 slices: entry k of row i at sptr[i / 32] + 32 k + i % 32,
+    // columns ascending; padding has column i, edge -1, value 0
+    const int32_t *sptr, *scol, *sedge;
+    double *sval;                            // coefficient of every slot (set per solve)
     const int32_t *agg;                      // -> next level (nullptr at the coarsest)
     const int32_t *mptr, *memb;              // members in the finer level (l > 0)
     const int32_t *iptr, *inner;             // finer-level edges inside the aggregate (l > 0)
@@ -162,7 +164,6 @@ struct AmgData {
     int grid = 0;             // cooperative grid size
     int n[kAmgMaxLev] = {}, ne[kAmgMaxLev] = {};
     AmgLevelDev *lev = nullptr;      // device copy of the level table
-    double *chol = nullptr;          // coarsest factor [nc * nc]
     int *coarse_ok = nullptr;
     double *z = nullptr, *p = nullptr, *q = nullptr, *r = nullptr;
     DeviceArena arena;
@@ -182,7 +183,6 @@ struct AmgArgs {
     const AmgLevelDev *lev;
     const double *d0, *o0;     // level-0 matrix: diagonal [N] and edge coefficients [F]
     double o0_sign;            // o = o0_sign * o0[f] (-1 when o0 holds the positive a_f)
-    double *chol;
     const double *b;
     double *x, *r, *z, *p, *q;
     double *partA, *partB;
@@ -207,9 +207,22 @@ struct Span {
 
 __device__ __forceinline__ Span grid_rows(int n)
 {
-    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    // whole 32-row slices per block, so a warp's rows share a slice
+    const int nsl = (n + 31) >> 5;
+    const int chunk = ((nsl + gridDim.x - 1) / gridDim.x) * 32;
     const int lo = min(n, (int)blockIdx.x * chunk);
     return {lo, min(n, lo + chunk)};
+}
+
+struct SRow {
+    int e0, K;
+};
+
+__device__ __forceinline__ SRow srow(const AmgLevelDev &L, int i)
+{
+    const int s = i >> 5;
+    const int p0 = L.sptr[s], p1 = L.sptr[s + 1];
+    return {p0 + (i & 31), (p1 - p0) >> 5};
 }
 
 __device__ __forceinline__ double coef(const AmgArgs &a, const AmgLevelDev &L, int l, int e)
@@ -227,8 +240,11 @@ __device__ __forceinline__ double row_ax(const AmgArgs &a, const AmgLevelDev &L,
                                          const double *x)
 {
     double t = diagv(a, L, l, i) * x[i];
-    const int e1 = L.rptr[i + 1];
-    for (int e = L.rptr[i]; e < e1; ++e) t += L.rv[e] * x[L.rcol[e]];
+    const SRow r = srow(L, i);
+    for (int k = 0; k < r.K; ++k) {
+        const int e = r.e0 + 32 * k;
+        t += L.sval[e] * x[L.scol[e]];
+    }
     return t;
 }
 
@@ -237,7 +253,14 @@ __device__ void phase_rows0(const AmgArgs &a, Span s, int t0, int step)
 {
     const AmgLevelDev &L = a.lev[0];
     for (int i = s.lo + t0; i < s.hi; i += step)
-        for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) L.rv[e] = coef(a, L, 0, L.redge[e]);
+    {
+        const SRow r = srow(L, i);
+        for (int k = 0; k < r.K; ++k) {
+            const int e = r.e0 + 32 * k;
+            const int E = L.sedge[e];
+            L.sval[e] = E < 0 ? 0.0 : coef(a, L, 0, E);
+        }
+    }
 }
 
 // ---- level phases over the rows [s.lo, s.hi) with thread stride `step` --
@@ -253,11 +276,14 @@ __device__ void phase_galerkin(const AmgArgs &a, int l, Span s, int t0, int step
         C.d[I] = v;
         C.dinv[I] = 1.0 / v;
         // the row's coefficients: the same sums as the edge phase below
-        for (int e = C.rptr[I]; e < C.rptr[I + 1]; ++e) {
-            const int E = C.redge[e];
+        const SRow r = srow(C, I);
+        for (int q = 0; q < r.K; ++q) {
+            const int e = r.e0 + 32 * q;
+            const int E = C.sedge[e];
             double w = 0.0;
-            for (int k = C.eptr[E]; k < C.eptr[E + 1]; ++k) w += coef(a, F, l - 1, C.elist[k]);
-            C.rv[e] = w;
+            if (E >= 0)
+                for (int k = C.eptr[E]; k < C.eptr[E + 1]; ++k) w += coef(a, F, l - 1, C.elist[k]);
+            C.sval[e] = w;
         }
     }
 }
@@ -306,27 +332,34 @@ __device__ void phase_prolong_sweep(const AmgArgs &a, int l, Span s, int t0, int
     for (int i = s.lo + t0; i < s.hi; i += step) {
         const double xi = L.xa[i] + kAmgAlpha * ec[L.agg[i]];
         double t = diagv(a, L, l, i) * xi;
-        for (int e = L.rptr[i]; e < L.rptr[i + 1]; ++e) {
-            const int j = L.rcol[e];
-            t += L.rv[e] * (L.xa[j] + kAmgAlpha * ec[L.agg[j]]);
+        const SRow r = srow(L, i);
+        for (int k = 0; k < r.K; ++k) {
+            const int e = r.e0 + 32 * k;
+            const int j = L.scol[e];
+            t += L.sval[e] * (L.xa[j] + kAmgAlpha * ec[L.agg[j]]);
         }
         L.x[i] = xi + kAmgOmega * (L.b[i] - t) * L.dinv[i];
     }
 }
 
 // Coarsest level: dense Cholesky factor (once per solve) by warp 0 of
-// block 0; returns false if the matrix is not positive definite.
-__device__ bool coarse_factor(const AmgArgs &a)
+// block 0, kept in block 0's shared memory `c` for the whole solve (every
+// step of the triangular solves then costs a shared-memory access, not an
+// L2 round trip); returns false if the matrix is not positive definite.
+__device__ bool coarse_factor(const AmgArgs &a, double *c)
 {
     const AmgLevelDev &C = a.lev[a.L];
     const int n = a.nc, lane = threadIdx.x & 31;
-    double *c = a.chol;
     for (int t = lane; t < n * n; t += 32) c[t] = 0.0;
     __syncwarp();
     for (int i = lane; i < n; i += 32) c[i * n + i] = diagv(a, C, a.L, i);
-    for (int i = lane; i < n; i += 32)
-        for (int e = C.rptr[i]; e < C.rptr[i + 1]; ++e)
-            c[i * n + C.rcol[e]] = C.rv[e];
+    for (int i = lane; i < n; i += 32) {
+        const SRow r = srow(C, i);
+        for (int k = 0; k < r.K; ++k) {
+            const int e = r.e0 + 32 * k;
+            if (C.sedge[e] >= 0) c[i * n + C.scol[e]] = C.sval[e];
+        }
+    }
     __syncwarp();
     bool ok = true;
     for (int j = 0; j < n; ++j) {
@@ -347,13 +380,12 @@ __device__ bool coarse_factor(const AmgArgs &a)
     return ok;
 }
 
-// xa_L = A_L^-1 b_L with the factor (warp 0 of block 0)
-__device__ void coarse_solve(const AmgArgs &a)
+// xa_L = A_L^-1 b_L with the factor c (shared memory; warp 0 of block 0),
+// working vector y in shared memory
+__device__ void coarse_solve(const AmgArgs &a, const double *c, double *y)
 {
     const AmgLevelDev &C = a.lev[a.L];
     const int n = a.nc, lane = threadIdx.x & 31;
-    const double *c = a.chol;
-    double *y = C.xa;
     for (int i = lane; i < n; i += 32) y[i] = C.b[i];
     __syncwarp();
     for (int k = 0; k < n; ++k) {            // forward: L y = b
@@ -370,10 +402,12 @@ __device__ void coarse_solve(const AmgArgs &a)
         if (lane == 0) y[k] = xk;
         __syncwarp();
     }
+    for (int i = lane; i < n; i += 32) C.xa[i] = y[i];
+    __syncwarp();
 }
 
 // The levels from G down to the coarsest and back, inside block 0.
-__device__ void block_levels_down_up(const AmgArgs &a)
+__device__ void block_levels_down_up(const AmgArgs &a, const double *chol, double *cy)
 {
     const int t0 = threadIdx.x, step = blockDim.x;
     for (int l = a.G; l < a.L; ++l) {
@@ -383,7 +417,7 @@ __device__ void block_levels_down_up(const AmgArgs &a)
         phase_restrict(a, l, Span{0, a.lev[l + 1].n}, t0, step);
         __syncthreads();
     }
-    if (threadIdx.x < 32) coarse_solve(a);
+    if (threadIdx.x < 32) coarse_solve(a, chol, cy);
     __syncthreads();
     for (int l = a.L - 1; l >= a.G; --l) {
         const Span s{0, a.lev[l].n};
@@ -400,6 +434,8 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
     __shared__ double tot[2];
     __shared__ AmgScal sc;
     __shared__ int s_coarse_ok;
+    __shared__ double s_chol[kAmgCoarseMax * kAmgCoarseMax];   // block 0: coarsest factor
+    __shared__ double s_cy[kAmgCoarseMax];
     const int t0 = threadIdx.x, step = blockDim.x;
     const AmgLevelDev &L0 = a.lev[0];
     const int N = L0.n;
@@ -427,7 +463,7 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
             __syncthreads();
         }
         if (threadIdx.x < 32) {
-            const bool cok = coarse_factor(a);
+            const bool cok = coarse_factor(a, s_chol);
             if (threadIdx.x == 0) s_coarse_ok = cok ? 1 : 0;
         }
         __syncthreads();
@@ -473,10 +509,10 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
             if (!ok) break;
             if (a.L == 0) {
                 // a single level: the exact solve
-                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve(a);
+                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve(a, s_chol, s_cy);
             } else {
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                if (blockIdx.x == 0) block_levels_down_up(a);
+                if (blockIdx.x == 0) block_levels_down_up(a, s_chol, s_cy);
             }
             double v1[1] = {0.0};
             for (int l = min(a.G, a.L) - 1; l >= 0; --l) {
@@ -567,17 +603,18 @@ fv_status upload(DeviceArena &ar, const T **d, const std::vector<T> &h)
     return FV_OK;
 }
 
-// rows of a graph: off-diagonal entries in ascending column (= ascending edge)
-void graph_rows(const Graph &g, std::vector<int32_t> &rptr, std::vector<int32_t> &rcol,
-                std::vector<int32_t> &redge)
+// Rows of a graph in SELL-32 slices: the off-diagonal entries of each row in
+// ascending column (= ascending edge), slot k of row i at
+// sptr[i / 32] + 32 k + i % 32; a slice is as wide as its longest row and
+// the padding slots hold column i and edge -1.
+void graph_sell(const Graph &g, std::vector<int32_t> &sptr, std::vector<int32_t> &scol,
+                std::vector<int32_t> &sedge)
 {
     const size_t ne = g.a.size();
-    rptr.assign(g.n + 1, 0);
+    std::vector<int32_t> rptr(g.n + 1, 0);
     for (size_t e = 0; e < ne; ++e) { ++rptr[g.a[e] + 1]; ++rptr[g.b[e] + 1]; }
     for (int i = 0; i < g.n; ++i) rptr[i + 1] += rptr[i];
-    rcol.resize(2 * ne);
-    redge.resize(2 * ne);
-    std::vector<int32_t> cur(rptr.begin(), rptr.end() - 1);
+    std::vector<int32_t> rcol(2 * ne), redge(2 * ne), cur(rptr.begin(), rptr.end() - 1);
     // edges are ordered by (a, b): for row i the edges with b == i (columns
     // a < i) come in ascending a, then those with a == i in ascending b
     for (size_t e = 0; e < ne; ++e) {
@@ -587,6 +624,27 @@ void graph_rows(const Graph &g, std::vector<int32_t> &rptr, std::vector<int32_t>
     for (size_t e = 0; e < ne; ++e) {
         const int i = g.a[e];
         rcol[cur[i]] = g.b[e]; redge[cur[i]++] = (int32_t)e;
+    }
+    const int nsl = (g.n + 31) / 32;
+    sptr.assign(nsl + 1, 0);
+    for (int sl = 0; sl < nsl; ++sl) {
+        int K = 0;
+        for (int i = 32 * sl; i < std::min(g.n, 32 * sl + 32); ++i) K = std::max(K, rptr[i + 1] - rptr[i]);
+        sptr[sl + 1] = sptr[sl] + 32 * K;
+    }
+    scol.assign(sptr[nsl], 0);
+    sedge.assign(sptr[nsl], -1);
+    for (int sl = 0; sl < nsl; ++sl) {
+        const int K = (sptr[sl + 1] - sptr[sl]) / 32;
+        for (int lane = 0; lane < 32; ++lane) {
+            const int i = 32 * sl + lane;
+            for (int k = 0; k < K; ++k) {
+                const int e = sptr[sl] + 32 * k + lane;
+                const bool real = i < g.n && k < rptr[i + 1] - rptr[i];
+                scol[e] = real ? rcol[rptr[i] + k] : (i < g.n ? i : 0);
+                sedge[e] = real ? redge[rptr[i] + k] : -1;
+            }
+        }
     }
 }
 
@@ -653,12 +711,12 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
         d.ne = (int)g[l].a.size();
         h->n[l] = d.n;
         h->ne[l] = d.ne;
-        std::vector<int32_t> rptr, rcol, redge;
-        graph_rows(g[l], rptr, rcol, redge);
-        if ((st = upload(ar, &d.rptr, rptr)) != FV_OK) return fail(st);
-        if ((st = upload(ar, &d.rcol, rcol)) != FV_OK) return fail(st);
-        if ((st = upload(ar, &d.redge, redge)) != FV_OK) return fail(st);
-        if ((st = ar.alloc_n(&d.rv, rcol.empty() ? 1 : rcol.size())) != FV_OK) return fail(st);
+        std::vector<int32_t> sptr, scol, sedge;
+        graph_sell(g[l], sptr, scol, sedge);
+        if ((st = upload(ar, &d.sptr, sptr)) != FV_OK) return fail(st);
+        if ((st = upload(ar, &d.scol, scol)) != FV_OK) return fail(st);
+        if ((st = upload(ar, &d.sedge, sedge)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.sval, scol.empty() ? 1 : scol.size())) != FV_OK) return fail(st);
         if (l < L && (st = upload(ar, &d.agg, agg[l])) != FV_OK) return fail(st);
         if (l > 0) {
             std::vector<int32_t> ptr, list, inner_key(g[l - 1].a.size(), -1);
@@ -686,7 +744,6 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
     if ((st = ar.alloc_n(&h->q, N)) != FV_OK) return fail(st);
     lv[0].b = h->r;            // level 0 smooths the CG residual
     h->z = lv[0].xa;
-    if ((st = ar.alloc_n(&h->chol, (size_t)g[L].n * g[L].n)) != FV_OK) return fail(st);
     if ((st = ar.alloc_n(&h->coarse_ok, 1)) != FV_OK) return fail(st);
     if ((st = ar.alloc_n(&h->lev, L + 1)) != FV_OK) return fail(st);
     FV_CUDA(cudaMemcpy(h->lev, lv.data(), sizeof(AmgLevelDev) * (L + 1), cudaMemcpyHostToDevice));
@@ -724,7 +781,6 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     a.d0 = pb.diag;
     a.o0 = pb.off;
     a.o0_sign = pb.off_sign;
-    a.chol = h->chol;
     a.b = pb.b;
     a.x = pb.x;
     a.r = h->r;
