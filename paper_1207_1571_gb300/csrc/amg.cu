@@ -43,7 +43,7 @@ constexpr int kAmgMaxLev = 24;
 constexpr int kAmgNmin = 32;           // coarsest level size target
 constexpr int kAmgCoarseMax = 64;      // largest coarsest level handled on the device
 constexpr int kAmgBlock = 512;
-constexpr int kAmgBlockRows = 1024;    // levels up to this size run inside block 0
+constexpr int kAmgBlockRows = 256;     // levels up to this size run inside block 0
 constexpr double kAmgTie = 1e-9;
 constexpr double kAmgOmega = 2.0 / 3.0;
 constexpr double kAmgAlpha = 1.8;
