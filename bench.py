@@ -52,7 +52,7 @@ REF_SAMPLE = "cavity3d_40"
 # ncu DRAM traffic (read + write bytes) per k_pcg launch, measured on the
 # workload named here; valid only for the kernel source it was taken on
 PCG_TRAFFIC = {"source_sha1": "d06177cf08e2eeceaaec8bb7186495c03130b8b4", "bytes_per_iter": 64209175,
-               "workload": "cavity3d_100, second pressure solve of the first step (789 iterations)"}
+               "workload": "cavity3d_100", "capture": "second pressure solve of the first step (789 iterations)"}
 
 
 def peaks():
@@ -297,7 +297,8 @@ def run_ours(args, ws, rank, local):
     achieved = bpi * iters_p / pcg_s / 1e9 if pcg_s > 0 else None
     traffic = None
     n_solves = max(1, len(per_solve))
-    if PCG_TRAFFIC["source_sha1"] == source_sha1() and PCG_TRAFFIC["bytes_per_iter"]:
+    if (PCG_TRAFFIC["source_sha1"] == source_sha1() and PCG_TRAFFIC["bytes_per_iter"]
+            and PCG_TRAFFIC["workload"] == args.workload):
         # per launch = per-iteration DRAM bytes x mean iterations per launch
         traffic = PCG_TRAFFIC["bytes_per_iter"] * iters_p / n_solves
     clk_sum = clk.summary()
