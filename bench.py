@@ -386,6 +386,32 @@ def run_ours(args, ws, rank, local):
                "us_per_iter": 1e3 * pa[4] / its_a if its_a else None,
                "rel_l2_vs_jacobi_cg": {"u": d_(ub, ua), "p": d_(pb_, pa_), "phi": d_(fb, fa)}}
         ca.close()
+        # and with the V-cycle in FP32 (a mixed-precision case)
+        cx = P.Case(mesh, w["nu"], P.FV_PREC_MIXED)
+        cx.set_pressure_solver(P.FV_PSOLVER_AMG)
+        for k in range(args.warmup):
+            step(k, h=cx.h)
+        cx.set_fields(*zero)
+        torch.cuda.synchronize()
+        evx = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        its_x = 0
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                evx[k][0].record(stream)
+            step(k, with_stats=False, h=cx.h)
+            with torch.cuda.stream(stream):
+                evx[k][1].record(stream)
+            its_x += sum(cx.last_stats()["iters"][3:])
+        torch.cuda.synchronize()
+        tx = allmax(ws, sum(x.elapsed_time(y) for x, y in evx) / 1e3, "cuda")
+        uc, pc, fc = cx.get_fields()
+        amg["fp32_cycle"] = {"value": ws * N * args.steps / tx, "unit": UNIT,
+                             "speedup_vs_jacobi_cg": t / tx, "cg_iterations": its_x,
+                             "rel_l2_vs_fp64_cycle": {"u": d_(uc, ub), "p": d_(pc, pb_),
+                                                      "phi": d_(fc, fb)}}
+        cx.close()
 
     # end to end through the C ABI with host buffers
     e2e = None

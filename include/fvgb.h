@@ -354,13 +354,22 @@ typedef enum { FV_PSOLVER_JACOBI = 0, FV_PSOLVER_AMG = 1 } fv_pressure_solver;
 fv_status fv_pcg_solve_amg(const fv_mesh *mesh, const double *diag, const double *upper,
                            const double *b, double *x, const fv_pcg_params *prm,
                            fv_solve_stats *stats);
+/* The same solve with the V-cycle in FP32 (level matrices, vectors and
+ * smoothing sweeps; the coarsest factor, the CG recurrences, its residual,
+ * reductions, stopping test and solution stay FP64).  The preconditioner
+ * changes by about 1e-7 relative, so iterates differ from fv_pcg_solve_amg
+ * at that level while the final FP64 residual meets the same tolerance. */
+fv_status fv_pcg_solve_amg_mixed(const fv_mesh *mesh, const double *diag, const double *upper,
+                                 const double *b, double *x, const fv_pcg_params *prm,
+                                 fv_solve_stats *stats);
 /* Build the hierarchy if needed; *n_levels and, if sizes is not NULL, the
  * node count of every level (sizes [n_levels], at most 24). */
 fv_status fv_amg_info(const fv_mesh *mesh, int32_t *n_levels, int32_t *sizes);
 /* Pressure solver of a case's PISO steps and SIMPLE iterations (default
  * FV_PSOLVER_JACOBI).  Selecting FV_PSOLVER_AMG builds the mesh's
  * hierarchy now (synchronous), so later steps may be captured in graphs;
- * FV_E_UNSUPPORTED for mixed-precision cases. */
+ * in a mixed-precision case the V-cycle runs in FP32
+ * (fv_pcg_solve_amg_mixed). */
 fv_status fv_case_set_pressure_solver(fv_case *cs, int32_t solver);
 /* Host only (no GPU): one coarsening level of a graph of n nodes and ne
  * edges (ea < eb, ordered by (ea, eb), weights ew > 0): agg [n] (node ->

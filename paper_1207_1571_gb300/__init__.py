@@ -181,6 +181,17 @@ class Mesh:
         check(rc, "fv_pcg_solve_amg", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
         return _solve_dict(st)
 
+    def pcg_solve_amg_mixed(self, diag, upper, b, x, tol=1e-6, reltol=0.0, maxit=10000) -> dict:
+        """Multigrid-preconditioned CG with the V-cycle in FP32 (fv_pcg_solve_amg_mixed)."""
+        prm = _capi.fv_pcg_params(tol, reltol, maxit, 0)
+        st = _capi.fv_solve_stats()
+        self._enter(diag, upper, b, x)
+        rc = self.L.fv_pcg_solve_amg_mixed(self.h, diag.data_ptr(), _ptr(upper), b.data_ptr(),
+                                           x.data_ptr(), C.byref(prm), C.byref(st))
+        self._leave()
+        check(rc, "fv_pcg_solve_amg_mixed", allow=(FV_E_NOT_CONVERGED, _capi.FV_E_DIVERGED))
+        return _solve_dict(st)
+
     def amg_levels(self) -> list:
         """Node count of every level of the multigrid hierarchy."""
         n = C.c_int32()

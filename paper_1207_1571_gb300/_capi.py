@@ -32,7 +32,7 @@ EXPORTS = [
     "fv_batch_run_graph", "fv_batch_get_fields", "fv_batch_schedule_info", "fv_batch_set_schedule",
     "fv_batch_autotune", "fv_ellj_build_host", "fv_ellj_create", "fv_ellj_destroy", "fv_ellj_info",
     "fv_ellj_from_ldu", "fv_ellj_spmv", "fv_pcg_solve_amg", "fv_amg_info",
-    "fv_case_set_pressure_solver", "fv_amg_coarsen_host",
+    "fv_case_set_pressure_solver", "fv_amg_coarsen_host", "fv_pcg_solve_amg_mixed",
 ]
 PROF_STAGES = ["momentum", "bicgstab", "hbya", "pressure", "pcg", "correct", "other"]
 
@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH):
         "fv_ellj_spmv": [vp, vp, vp, vp, vp, i32],
         "fv_pcg_solve_amg": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_amg_info": [vp, vp, vp],
+        "fv_pcg_solve_amg_mixed": [vp, vp, vp, vp, vp, P(fv_pcg_params), P(fv_solve_stats)],
         "fv_case_set_pressure_solver": [vp, i32],
         "fv_amg_coarsen_host": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "fv_set_barrier_spin_limit": [C.c_int64],

@@ -154,8 +154,10 @@ struct AmgLevelDev {
     const int32_t *mptr, *memb;              // members in the finer level (l > 0)
     const int32_t *iptr, *inner;             // finer-level edges inside the aggregate (l > 0)
     const int32_t *eptr, *elist;             // finer-level edges of each edge (l > 0)
-    double *d, *o, *dinv;                    // matrix (level 0: d and o unused)
+    double *d, *o, *dinv;                    // matrix (level 0: d copied per solve, o unused)
     double *b, *x, *xa;                      // right-hand side, iterates
+    // FP32 copies the cycle smooths with in mixed precision
+    float *sval32, *d32, *dinv32, *b32, *x32, *xa32;
 };
 
 struct AmgData {
@@ -183,6 +185,7 @@ struct AmgArgs {
     const AmgLevelDev *lev;
     const double *d0, *o0;     // level-0 matrix: diagonal [N] and edge coefficients [F]
     double o0_sign;            // o = o0_sign * o0[f] (-1 when o0 holds the positive a_f)
+    int fp32;                  // the V-cycle in FP32 (mixed precision)
     const double *b;
     double *x, *r, *z, *p, *q;
     double *partA, *partB;
@@ -248,17 +251,59 @@ __device__ __forceinline__ double row_ax(const AmgArgs &a, const AmgLevelDev &L,
     return t;
 }
 
-// level 0's per-entry coefficients from the caller's edge array
+// The arrays a V-cycle in value type V works on (FP64, or the FP32 copies).
+template <class V> struct VL;
+template <> struct VL<double> {
+    __device__ static const double *sval(const AmgLevelDev &L) { return L.sval; }
+    __device__ static const double *d(const AmgLevelDev &L) { return L.d; }
+    __device__ static const double *dinv(const AmgLevelDev &L) { return L.dinv; }
+    __device__ static double *b(const AmgLevelDev &L) { return L.b; }
+    __device__ static double *x(const AmgLevelDev &L) { return L.x; }
+    __device__ static double *xa(const AmgLevelDev &L) { return L.xa; }
+};
+template <> struct VL<float> {
+    __device__ static const float *sval(const AmgLevelDev &L) { return L.sval32; }
+    __device__ static const float *d(const AmgLevelDev &L) { return L.d32; }
+    __device__ static const float *dinv(const AmgLevelDev &L) { return L.dinv32; }
+    __device__ static float *b(const AmgLevelDev &L) { return L.b32; }
+    __device__ static float *x(const AmgLevelDev &L) { return L.x32; }
+    __device__ static float *xa(const AmgLevelDev &L) { return L.xa32; }
+};
+
+// (A x)_i on a level in the cycle's value type
+template <class V>
+__device__ __forceinline__ V row_axv(const AmgLevelDev &L, int i, const V *x)
+{
+    const V *sv = VL<V>::sval(L);
+    V t = VL<V>::d(L)[i] * x[i];
+    const SRow r = srow(L, i);
+    for (int k = 0; k < r.K; ++k) {
+        const int e = r.e0 + 32 * k;
+        t += sv[e] * x[L.scol[e]];
+    }
+    return t;
+}
+
+// Level 0 per solve: per-entry coefficients from the caller's edge array,
+// the diagonal and its reciprocal (and their FP32 copies in mixed precision).
 __device__ void phase_rows0(const AmgArgs &a, Span s, int t0, int step)
 {
     const AmgLevelDev &L = a.lev[0];
-    for (int i = s.lo + t0; i < s.hi; i += step)
-    {
+    for (int i = s.lo + t0; i < s.hi; i += step) {
+        const double d = a.d0[i];
+        L.d[i] = d;
+        L.dinv[i] = 1.0 / d;
+        if (a.fp32) {
+            L.d32[i] = (float)d;
+            L.dinv32[i] = (float)(1.0 / d);
+        }
         const SRow r = srow(L, i);
         for (int k = 0; k < r.K; ++k) {
             const int e = r.e0 + 32 * k;
             const int E = L.sedge[e];
-            L.sval[e] = E < 0 ? 0.0 : coef(a, L, 0, E);
+            const double v = E < 0 ? 0.0 : coef(a, L, 0, E);
+            L.sval[e] = v;
+            if (a.fp32) L.sval32[e] = (float)v;
         }
     }
 }
@@ -275,6 +320,10 @@ __device__ void phase_galerkin(const AmgArgs &a, int l, Span s, int t0, int step
         for (int k = C.iptr[I]; k < C.iptr[I + 1]; ++k) v += 2.0 * coef(a, F, l - 1, C.inner[k]);
         C.d[I] = v;
         C.dinv[I] = 1.0 / v;
+        if (a.fp32) {
+            C.d32[I] = (float)v;
+            C.dinv32[I] = (float)(1.0 / v);
+        }
         // the row's coefficients: the same sums as the edge phase below
         const SRow r = srow(C, I);
         for (int q = 0; q < r.K; ++q) {
@@ -284,6 +333,7 @@ __device__ void phase_galerkin(const AmgArgs &a, int l, Span s, int t0, int step
             if (E >= 0)
                 for (int k = C.eptr[E]; k < C.eptr[E + 1]; ++k) w += coef(a, F, l - 1, C.elist[k]);
             C.sval[e] = w;
+            if (a.fp32) C.sval32[e] = (float)w;
         }
     }
 }
@@ -299,46 +349,57 @@ __device__ void phase_galerkin_edges(const AmgArgs &a, int l, Span s, int t0, in
 }
 
 // x = x + omega (b - A x) / d, from xin to xout
-__device__ void phase_sweep(const AmgArgs &a, int l, const double *xin, double *xout, Span s,
-                            int t0, int step)
+template <class V>
+__device__ void phase_sweep(const AmgArgs &a, int l, const V *xin, V *xout, Span s, int t0,
+                            int step)
 {
     const AmgLevelDev &L = a.lev[l];
+    const V *b = VL<V>::b(L), *dinv = VL<V>::dinv(L);
+    const V w = (V)kAmgOmega;
     for (int i = s.lo + t0; i < s.hi; i += step)
-        xout[i] = xin[i] + kAmgOmega * (L.b[i] - row_ax(a, L, l, i, xin)) * L.dinv[i];
+        xout[i] = xin[i] + w * (b[i] - row_axv<V>(L, i, xin)) * dinv[i];
 }
 
 // b_{l+1} = P^T (b - A xa) over each aggregate, and the next level's first
 // sweep from zero: x_{l+1} = omega b_{l+1} / d_{l+1}.
+template <class V>
 __device__ void phase_restrict(const AmgArgs &a, int l, Span s, int t0, int step)
 {
     const AmgLevelDev &F = a.lev[l], &C = a.lev[l + 1];
+    const V *fb = VL<V>::b(F), *fxa = VL<V>::xa(F), *cdinv = VL<V>::dinv(C);
+    V *cb = VL<V>::b(C), *cx = VL<V>::x(C);
     for (int I = s.lo + t0; I < s.hi; I += step) {
-        double v = 0.0;
+        V v = 0;
         for (int k = C.mptr[I]; k < C.mptr[I + 1]; ++k) {
             const int i = C.memb[k];
-            v += F.b[i] - row_ax(a, F, l, i, F.xa);
+            v += fb[i] - row_axv<V>(F, i, fxa);
         }
-        C.b[I] = v;
-        C.x[I] = kAmgOmega * v * C.dinv[I];
+        cb[I] = v;
+        cx[I] = (V)kAmgOmega * v * cdinv[I];
     }
 }
 
 // x = xa + alpha P e_c, then one sweep; neighbours' prolonged values are
 // formed on the fly.
+template <class V>
 __device__ void phase_prolong_sweep(const AmgArgs &a, int l, Span s, int t0, int step)
 {
     const AmgLevelDev &L = a.lev[l];
-    const double *ec = a.lev[l + 1].xa;
+    const V *ec = VL<V>::xa(a.lev[l + 1]);
+    const V *xa = VL<V>::xa(L), *sv = VL<V>::sval(L), *d = VL<V>::d(L);
+    const V *b = VL<V>::b(L), *dinv = VL<V>::dinv(L);
+    V *x = VL<V>::x(L);
+    const V al = (V)kAmgAlpha;
     for (int i = s.lo + t0; i < s.hi; i += step) {
-        const double xi = L.xa[i] + kAmgAlpha * ec[L.agg[i]];
-        double t = diagv(a, L, l, i) * xi;
+        const V xi = xa[i] + al * ec[L.agg[i]];
+        V t = d[i] * xi;
         const SRow r = srow(L, i);
         for (int k = 0; k < r.K; ++k) {
             const int e = r.e0 + 32 * k;
             const int j = L.scol[e];
-            t += L.sval[e] * (L.xa[j] + kAmgAlpha * ec[L.agg[j]]);
+            t += sv[e] * (xa[j] + al * ec[L.agg[j]]);
         }
-        L.x[i] = xi + kAmgOmega * (L.b[i] - t) * L.dinv[i];
+        x[i] = xi + (V)kAmgOmega * (b[i] - t) * dinv[i];
     }
 }
 
@@ -380,13 +441,16 @@ __device__ bool coarse_factor(const AmgArgs &a, double *c)
     return ok;
 }
 
-// xa_L = A_L^-1 b_L with the factor c (shared memory; warp 0 of block 0),
-// working vector y in shared memory
+// xa_L = A_L^-1 b_L with the FP64 factor c (shared memory; warp 0 of block
+// 0), working vector y in shared memory
+template <class V>
 __device__ void coarse_solve(const AmgArgs &a, const double *c, double *y)
 {
     const AmgLevelDev &C = a.lev[a.L];
     const int n = a.nc, lane = threadIdx.x & 31;
-    for (int i = lane; i < n; i += 32) y[i] = C.b[i];
+    const V *cb = VL<V>::b(C);
+    V *cxa = VL<V>::xa(C);
+    for (int i = lane; i < n; i += 32) y[i] = (double)cb[i];
     __syncwarp();
     for (int k = 0; k < n; ++k) {            // forward: L y = b
         const double yk = y[k] / c[k * n + k];
@@ -402,32 +466,52 @@ __device__ void coarse_solve(const AmgArgs &a, const double *c, double *y)
         if (lane == 0) y[k] = xk;
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) C.xa[i] = y[i];
+    for (int i = lane; i < n; i += 32) cxa[i] = (V)y[i];
     __syncwarp();
 }
 
 // The levels from G down to the coarsest and back, inside block 0.
+template <class V>
 __device__ void block_levels_down_up(const AmgArgs &a, const double *chol, double *cy)
 {
     const int t0 = threadIdx.x, step = blockDim.x;
     for (int l = a.G; l < a.L; ++l) {
         const Span s{0, a.lev[l].n};
-        phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, s, t0, step);
+        phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]), s, t0, step);
         __syncthreads();
-        phase_restrict(a, l, Span{0, a.lev[l + 1].n}, t0, step);
+        phase_restrict<V>(a, l, Span{0, a.lev[l + 1].n}, t0, step);
         __syncthreads();
     }
-    if (threadIdx.x < 32) coarse_solve(a, chol, cy);
+    if (threadIdx.x < 32) coarse_solve<V>(a, chol, cy);
     __syncthreads();
     for (int l = a.L - 1; l >= a.G; --l) {
         const Span s{0, a.lev[l].n};
-        phase_prolong_sweep(a, l, s, t0, step);
+        phase_prolong_sweep<V>(a, l, s, t0, step);
         __syncthreads();
-        phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, s, t0, step);
+        phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]), s, t0, step);
         __syncthreads();
     }
 }
 
+// Level 0's right-hand side is the CG residual r; the first pre-smoothing
+// sweep from zero is x = omega r / d.  In FP32 the residual is rounded into
+// the cycle's own right-hand side.
+template <class V>
+__device__ __forceinline__ void seed0(const AmgLevelDev &L0, int i, double ri);
+template <>
+__device__ __forceinline__ void seed0<double>(const AmgLevelDev &L0, int i, double ri)
+{
+    L0.x[i] = kAmgOmega * ri * L0.dinv[i];
+}
+template <>
+__device__ __forceinline__ void seed0<float>(const AmgLevelDev &L0, int i, double ri)
+{
+    const float b = (float)ri;
+    L0.b32[i] = b;
+    L0.x32[i] = (float)kAmgOmega * b * L0.dinv32[i];
+}
+
+template <class V>
 __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
 {
     __shared__ double buf[2][kAmgBlock];
@@ -444,9 +528,8 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
     bool ok = true;
     int it = 0;
 
-    // ---- setup: 1/diag and row coefficients on level 0, Galerkin matrices,
-    // coarsest factor
-    for (int i = s0.lo + t0; i < s0.hi; i += step) L0.dinv[i] = 1.0 / a.d0[i];
+    // ---- setup: diagonal and row coefficients on level 0, Galerkin
+    // matrices, coarsest factor
     phase_rows0(a, s0, t0, step);
     for (int l = 1; l < a.G && l <= a.L && ok; ++l) {
         ok = grid_sync(a.bar, gen, a.spin);
@@ -477,7 +560,7 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
             const double bi = a.b[i];
             const double ri = bi - row_ax(a, L0, 0, i, a.x);
             a.r[i] = ri;
-            L0.x[i] = kAmgOmega * ri * L0.dinv[i];      // first pre-smoothing sweep
+            seed0<V>(L0, i, ri);                         // first pre-smoothing sweep
             v[0] += bi * bi;
             v[1] += ri * ri;
         }
@@ -502,29 +585,32 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
                 // (the barrier before the first sweep of level 0 is the one
                 // that ended the previous phase)
                 if (l > 0 && !(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, grid_rows(a.lev[l].n), t0, step);
+                phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]),
+                               grid_rows(a.lev[l].n), t0, step);
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_restrict(a, l, grid_rows(a.lev[l + 1].n), t0, step);
+                phase_restrict<V>(a, l, grid_rows(a.lev[l + 1].n), t0, step);
             }
             if (!ok) break;
             if (a.L == 0) {
                 // a single level: the exact solve
-                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve(a, s_chol, s_cy);
+                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve<V>(a, s_chol, s_cy);
             } else {
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                if (blockIdx.x == 0) block_levels_down_up(a, s_chol, s_cy);
+                if (blockIdx.x == 0) block_levels_down_up<V>(a, s_chol, s_cy);
             }
             double v1[1] = {0.0};
             for (int l = min(a.G, a.L) - 1; l >= 0; --l) {
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_prolong_sweep(a, l, grid_rows(a.lev[l].n), t0, step);
+                phase_prolong_sweep<V>(a, l, grid_rows(a.lev[l].n), t0, step);
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_sweep(a, l, a.lev[l].x, a.lev[l].xa, grid_rows(a.lev[l].n), t0, step);
+                phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]),
+                               grid_rows(a.lev[l].n), t0, step);
             }
             if (!ok) break;
             if (a.L == 0 && !(ok = grid_sync(a.bar, gen, a.spin))) break;
-            // rho = r.z (z = level 0's xa)
-            for (int i = s0.lo + t0; i < s0.hi; i += step) v1[0] += a.r[i] * L0.xa[i];
+            // rho = r.z (z = level 0's xa, in FP64)
+            const V *z = VL<V>::xa(L0);
+            for (int i = s0.lo + t0; i < s0.hi; i += step) v1[0] += a.r[i] * (double)z[i];
             if (!(ok = cg_grid_sum<1, kAmgBlock>(v1, a.partA, a.bar, gen, a.spin, buf, tot))) break;
             ++it;
             if (threadIdx.x == 0) {
@@ -538,7 +624,7 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
             // ---- p = z + beta p
             const double beta = sc.beta;
             for (int i = s0.lo + t0; i < s0.hi; i += step)
-                a.p[i] = it == 1 ? L0.xa[i] : L0.xa[i] + beta * a.p[i];
+                a.p[i] = it == 1 ? (double)z[i] : (double)z[i] + beta * a.p[i];
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
             // ---- q = A p, p.q
             double v2[1] = {0.0};
@@ -562,7 +648,7 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
                 a.x[i] += alpha * a.p[i];
                 const double ri = a.r[i] - alpha * a.q[i];
                 a.r[i] = ri;
-                L0.x[i] = kAmgOmega * ri * L0.dinv[i];
+                seed0<V>(L0, i, ri);
                 v3[0] += ri * ri;
             }
             if (!(ok = cg_grid_sum<1, kAmgBlock>(v3, a.partA, a.bar, gen, a.spin, buf, tot))) break;
@@ -731,10 +817,17 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
             group(d.ne, emap[l - 1], ptr, list);
             if ((st = upload(ar, &d.eptr, ptr)) != FV_OK) return fail(st);
             if ((st = upload(ar, &d.elist, list)) != FV_OK) return fail(st);
-            if ((st = ar.alloc_n(&d.d, d.n)) != FV_OK) return fail(st);
             if ((st = ar.alloc_n(&d.o, d.ne ? d.ne : 1)) != FV_OK) return fail(st);
         }
+        if ((st = ar.alloc_n(&d.d, d.n)) != FV_OK) return fail(st);
         if ((st = ar.alloc_n(&d.dinv, d.n)) != FV_OK) return fail(st);
+        // FP32 copies for the mixed-precision cycle
+        if ((st = ar.alloc_n(&d.sval32, scol.empty() ? 1 : scol.size())) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.d32, d.n)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.dinv32, d.n)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.b32, d.n)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.x32, d.n)) != FV_OK) return fail(st);
+        if ((st = ar.alloc_n(&d.xa32, d.n)) != FV_OK) return fail(st);
         if (l > 0 && (st = ar.alloc_n(&d.b, d.n)) != FV_OK) return fail(st);
         if ((st = ar.alloc_n(&d.x, d.n)) != FV_OK) return fail(st);
         if ((st = ar.alloc_n(&d.xa, d.n)) != FV_OK) return fail(st);
@@ -748,7 +841,10 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
     if ((st = ar.alloc_n(&h->lev, L + 1)) != FV_OK) return fail(st);
     FV_CUDA(cudaMemcpy(h->lev, lv.data(), sizeof(AmgLevelDev) * (L + 1), cudaMemcpyHostToDevice));
     int per_sm = 0;
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_amg, kAmgBlock, 0));
+    int per_sm32 = 0;
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_amg<double>, kAmgBlock, 0));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_pcg_amg<float>, kAmgBlock, 0));
+    per_sm = std::min(per_sm, per_sm32);
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "multigrid CG kernel cannot be resident");
     h->grid = m->sm_count * std::min(per_sm, 2);
     *out = h;
@@ -781,6 +877,7 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     a.d0 = pb.diag;
     a.o0 = pb.off;
     a.o0_sign = pb.off_sign;
+    a.fp32 = pb.fp32;
     a.b = pb.b;
     a.x = pb.x;
     a.r = h->r;
@@ -811,7 +908,8 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {&a};
-    FV_CUDA(cudaLaunchKernelExC(&cfg, (const void *)k_pcg_amg, args));
+    const void *fn = pb.fp32 ? (const void *)k_pcg_amg<float> : (const void *)k_pcg_amg<double>;
+    FV_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
     return FV_OK;
 }
 

@@ -66,8 +66,10 @@ fv_status launch_pressure_solve(const fv_case *c, double tol, double reltol, int
                                 DevSolveStats *st)
 {
     if (c->psolver == FV_PSOLVER_AMG) {
-        // the face coefficients a_f of the pressure assembly are -upper
-        AmgProblem ap{c->Pd, c->af, -1.0, c->pbv, c->p, tol, reltol, maxit, st};
+        // the face coefficients a_f of the pressure assembly are -upper; a
+        // mixed-precision case smooths in FP32
+        AmgProblem ap{c->Pd, c->af, -1.0, c->pbv, c->p, tol, reltol, maxit, st,
+                      c->precision == FV_PREC_MIXED ? 1 : 0};
         return launch_pcg_amg(c->mesh, ap);
     }
     if (c->precision == FV_PREC_MIXED) {
@@ -484,9 +486,9 @@ extern "C" fv_status fv_pcg_solve(const fv_mesh *mc, const double *diag, const d
     return (fv_status)h.status;
 }
 
-extern "C" fv_status fv_pcg_solve_amg(const fv_mesh *mc, const double *diag, const double *upper,
-                                      const double *b, double *x, const fv_pcg_params *prm,
-                                      fv_solve_stats *stats)
+static fv_status pcg_solve_amg(const fv_mesh *mc, const double *diag, const double *upper,
+                               const double *b, double *x, const fv_pcg_params *prm,
+                               fv_solve_stats *stats, int fp32)
 {
     FV_CHECK(mc && diag && b && x && prm, FV_E_INVALID, "NULL argument");
     FV_CHECK(mc->F == 0 || upper, FV_E_INVALID, "upper is NULL");
@@ -494,7 +496,7 @@ extern "C" fv_status fv_pcg_solve_amg(const fv_mesh *mc, const double *diag, con
     fv_mesh *m = const_cast<fv_mesh *>(mc);
     fv_status st = amg_prepare(m);
     if (st != FV_OK) return st;
-    AmgProblem ap{diag, upper, 1.0, b, x, prm->tol, prm->reltol, prm->maxit, m->kw.stats};
+    AmgProblem ap{diag, upper, 1.0, b, x, prm->tol, prm->reltol, prm->maxit, m->kw.stats, fp32};
     if ((st = launch_pcg_amg(m, ap)) != FV_OK) return st;
     DevSolveStats h;
     FV_CUDA(cudaMemcpyAsync(&h, m->kw.stats, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
@@ -503,13 +505,25 @@ extern "C" fv_status fv_pcg_solve_amg(const fv_mesh *mc, const double *diag, con
     return (fv_status)h.status;
 }
 
+extern "C" fv_status fv_pcg_solve_amg(const fv_mesh *mc, const double *diag, const double *upper,
+                                      const double *b, double *x, const fv_pcg_params *prm,
+                                      fv_solve_stats *stats)
+{
+    return pcg_solve_amg(mc, diag, upper, b, x, prm, stats, 0);
+}
+
+extern "C" fv_status fv_pcg_solve_amg_mixed(const fv_mesh *mc, const double *diag,
+                                            const double *upper, const double *b, double *x,
+                                            const fv_pcg_params *prm, fv_solve_stats *stats)
+{
+    return pcg_solve_amg(mc, diag, upper, b, x, prm, stats, 1);
+}
+
 extern "C" fv_status fv_case_set_pressure_solver(fv_case *c, int32_t solver)
 {
     FV_CHECK(c, FV_E_INVALID, "NULL case");
     FV_CHECK(solver == FV_PSOLVER_JACOBI || solver == FV_PSOLVER_AMG, FV_E_INVALID,
              "unknown pressure solver %d", solver);
-    FV_CHECK(solver == FV_PSOLVER_JACOBI || c->precision == FV_PREC_FP64, FV_E_UNSUPPORTED,
-             "the multigrid pressure solver runs in FP64 only");
     if (solver == FV_PSOLVER_AMG) {
         fv_status st = amg_prepare(const_cast<fv_mesh *>(c->mesh));
         if (st != FV_OK) return st;

@@ -115,6 +115,7 @@ struct AmgProblem {
     double tol, reltol;
     int maxit;
     DevSolveStats *stats;    // device
+    int fp32 = 0;            // V-cycle in FP32 (mixed precision)
 };
 
 }  // namespace fvgb

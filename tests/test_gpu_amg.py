@@ -247,10 +247,64 @@ def test_simple_with_amg(P):
 def test_amg_pressure_solver_rules(P):
     m = mg.cavity2d(8)
     mesh = P.Mesh(m)
-    with pytest.raises(P.FvError):
-        P.Case(mesh, 0.1, P.FV_PREC_MIXED).set_pressure_solver(P.FV_PSOLVER_AMG)
+    P.Case(mesh, 0.1, P.FV_PREC_MIXED).set_pressure_solver(P.FV_PSOLVER_AMG)
     with pytest.raises(P.FvError):
         P.Case(mesh, 0.1).set_pressure_solver(7)
+
+
+@pytest.mark.parametrize("which", ["3d", "3d_big", "tp"])
+def test_amg_mixed_solve_meets_fp64_residual(P, which):
+    """The V-cycle in FP32: the final FP64 residual (the oracle's product)
+    meets the tolerance, the solution is as close to the FP64 multigrid
+    solution as the tolerance allows, in about as many iterations."""
+    m, om, d, up, b = system(which)
+    own, nei = om.addressing()
+    amg = O.Amg(om)
+    mesh = P.Mesh(m, renumber=True)
+    for tol in (1e-6, 1e-10):
+        xo, ito, _, _, _ = amg.pcg(d, up, b, np.zeros(m.n_cells), tol=tol)
+        x = t64(np.zeros(m.n_cells))
+        s = mesh.pcg_solve_amg_mixed(t64(d), t64(up), t64(b), x, tol=tol)
+        xg = x.cpu().numpy()
+        assert s["status"] == 0
+        r = b - O.ldu_matvec(own, nei, d, up, up, xg)
+        assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * (1 + 1e-6)
+        assert s["iters"] <= ito + max(2, ito // 4), (s["iters"], ito)
+        pinned = which != "tp"
+        a_, b_ = (xg - xg.mean(), xo - xo.mean()) if pinned else (xg, xo)
+        assert rel(a_, b_) <= 1e3 * tol, rel(a_, b_)
+
+
+@pytest.mark.parametrize("which", ["3d", "tp"])
+def test_piso_with_mixed_amg_against_fp64_oracle(P, which):
+    """PISO steps of a mixed-precision case with the multigrid pressure
+    solver (FP32 V-cycle) against the FP64 oracle with the FP64 multigrid
+    solver: every pressure solve meets the FP64 tolerance; fields agree to
+    about the solver tolerance."""
+    if which == "3d":
+        m, nu, dt, steps = mg.permute_cells(mg.cavity3d(14), mg.random_permutation(14 ** 3, 2)), 0.01, 0.01, 8
+        ref = m.corner_cell
+    else:
+        m, nu, dt, steps = mg.tp_channel(320, 30), 3.3e-6, 1e-4, 10
+        ref = -1
+    mesh = P.Mesh(m, renumber=True)
+    case = P.Case(mesh, nu, P.FV_PREC_MIXED)
+    case.set_pressure_solver(P.FV_PSOLVER_AMG)
+    oc = O.Case(O.Mesh(m, renumber=True), nu)
+    oc.set_pressure_solver(1)
+    for k in range(steps):
+        for c in (case, oc):
+            if which == "tp":
+                c.set_patch(m.patch("inlet"), mg.tp_inlet((k + 1) * dt), 0.0)
+        s = case.piso_step(dt, 2, p_ref_cell=ref)
+        oc.piso_step(dt, 2, p_ref_cell=ref)
+        assert s["status"] == 0 and all(x["res"] <= 1e-6 for x in s["p"]), s["p"]
+    (u, p, phi), (uo, po, phio) = case.get_fields_host(), oc.get_fields()
+    if ref >= 0:
+        p, po = p - p.mean(), po - po.mean()
+    eu, ep, ef = rel(u, uo), rel(p, po), rel(phi, phio)
+    print(f"mixed multigrid vs FP64 oracle after {steps} steps: u {eu:.2e} p {ep:.2e} phi {ef:.2e}")
+    assert eu < 1e-4 and ep < 1e-3 and ef < 1e-4
 
 
 def test_full_size_cavity_first_step_with_amg(P):
