@@ -108,3 +108,52 @@ def test_tp_full_size_startup_profile(P, full_mesh):
     dz = m.V[0] / (h * TP["H"] / TP["ny"])
     assert -fin / dz == pytest.approx(S.Q(T), rel=1e-12)
     assert fout == pytest.approx(-fin, rel=1e-5)
+
+
+def test_tp1m_all_5000_steps_with_multigrid(P, full_mesh):
+    """The paper's whole tp1M run: 5000 PISO steps of 0.1 ms (to t = 0.5 s,
+    a quarter period of the inlet), pressure by the multigrid CG with the
+    FP32 V-cycle.  At the end the flow in the middle of the pipe is the
+    exact start-up solution (Stokes layers 1.3 mm = 19 cells thick by
+    then), the pressure gradient matches, and the pipe passes the inlet's
+    flow rate."""
+    import time
+    import torch
+    from womersley import StartupChannel
+    m = full_mesh
+    case = P.Case(P.Mesh(m, renumber=True), TP["nu"], P.FV_PREC_MIXED)
+    case.set_pressure_solver(P.FV_PSOLVER_AMG)
+    steps = TP["steps"]
+    its = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n in range(steps):
+        tp_step(case, m, n, stats=False)
+        if n % 250 == 249:
+            st = case.last_stats()
+            assert st["status"] == 0, (n, st)
+            its += sum(st["iters"][3:])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    u, p, phi = case.get_fields_host()
+    T = steps * TP["dt"]
+    S = StartupChannel(TP["H"], TP["nu"], TP["u0"], 2 * np.pi * TP["f"])
+    nx, h = TP["nx"], TP["L"] / TP["nx"]
+    i = np.arange(m.n_cells) % nx
+    errs = []
+    for a in (nx // 4, nx // 2 - 1, 3 * nx // 4):
+        y = m.C[1][i == a]
+        errs.append(rel(u[0][i == a], S.u(y, T)))
+    a, b = nx // 2 - 1, nx // 2
+    G = -(p[i == b] - p[i == a]).mean() / h
+    print(f"tp1M 5000 steps in {wall:.1f} s wall; CG iterations of every 250th step: {its}; "
+          f"profile errors {['%.2e' % e for e in errs]}; dp/dx error {abs(G / S.G(T) - 1):.2e}")
+    assert max(errs) < 5e-4          # measured 6.7e-5
+    assert G == pytest.approx(S.G(T), rel=1e-2)     # measured 2.6e-3
+    F = m.n_internal_faces
+    inl, out = m.patches[m.patch("inlet")], m.patches[m.patch("outlet")]
+    fin = phi[F + inl.start:F + inl.start + inl.size].sum()
+    fout = phi[F + out.start:F + out.start + out.size].sum()
+    dz = m.V[0] / (h * TP["H"] / TP["ny"])
+    assert -fin / dz == pytest.approx(S.Q(T), rel=1e-12)
+    assert fout == pytest.approx(-fin, rel=1e-5)
