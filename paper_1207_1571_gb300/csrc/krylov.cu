@@ -270,24 +270,36 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             if (it == 1) {
                 for (int i = i0; i < re; i += kCgBlock) a.p[i] = a.r[i];
             } else {
+                // restrict-qualified copies and all three loads before the
+                // two stores: several rows' loads stay in flight at once
+                // (with y += alpha p written as a load-modify-store first,
+                // this pass ran at 62 % of the copy bandwidth instead of 80 %)
                 const double alpha = sc.alpha, beta = sc.beta;
-#pragma unroll 2
+                double *__restrict__ yv = a.y;
+                double *__restrict__ pv = a.p;
+                const double *__restrict__ rv = a.r;
+#pragma unroll 4
                 for (int i = i0; i < re; i += kCgBlock) {
-                    const double po = a.p[i];
-                    a.y[i] += alpha * po;
-                    a.p[i] = a.r[i] + beta * po;
+                    const double po = pv[i];
+                    const double ri = rv[i];
+                    const double yi = yv[i];
+                    pv[i] = ri + beta * po;
+                    yv[i] = yi + alpha * po;
                 }
             }
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
             // P2: q = A^ p (unit diagonal), p.q
             double v1[1] = {0.0};
+            {
+                double *__restrict__ qv = a.q;
 #pragma unroll 2
-            for (int i = i0; i < re; i += kCgBlock) {
-                const RowSpan rs = row_span(a.slice_ptr, i);
-                const double pi = a.p[i];
-                const double acc = spmv_unit_row(a, rs, pi);
-                a.q[i] = acc;
-                v1[0] += pi * acc;
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const RowSpan rs = row_span(a.slice_ptr, i);
+                    const double pi = a.p[i];
+                    const double acc = spmv_unit_row(a, rs, pi);
+                    qv[i] = acc;
+                    v1[0] += pi * acc;
+                }
             }
             if (!(ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf, tot))) break;
             if (threadIdx.x == 0) {
@@ -301,12 +313,29 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             const double alpha = sc.alpha;
             const bool exact = sc.exact || it >= a.maxit;
             double v2[2] = {0.0, 0.0};
-#pragma unroll 2
-            for (int i = i0; i < re; i += kCgBlock) {
-                const double ri = a.r[i] - alpha * a.q[i];
-                a.r[i] = ri;
-                v2[0] += ri * ri;
-                if (exact) v2[1] += (a.diag[i] * ri) * ri;
+            {
+                double *__restrict__ rv = a.r;
+                const double *__restrict__ qv = a.q;
+                const double *__restrict__ dv = a.diag;
+                if (exact) {
+                    for (int i = i0; i < re; i += kCgBlock) {
+                        const double ri = rv[i] - alpha * qv[i];
+                        rv[i] = ri;
+                        v2[0] += ri * ri;
+                        v2[1] += (dv[i] * ri) * ri;
+                    }
+                } else {
+                    // the common case, a tight loop (a uniform branch inside the
+                    // unrolled loop cost a third of this pass's bandwidth)
+                    double acc = 0.0;
+#pragma unroll 4
+                    for (int i = i0; i < re; i += kCgBlock) {
+                        const double ri = rv[i] - alpha * qv[i];
+                        rv[i] = ri;
+                        acc += ri * ri;
+                    }
+                    v2[0] = acc;
+                }
             }
             if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
             if (threadIdx.x == 0) {
@@ -553,11 +582,16 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             if (sc.restart) {
                 for (int i = i0; i < re; i += kCgBlock) a.p[i] = fmaf(-delta, a.w[i], a.r[i]);
             } else {
-#pragma unroll 2
+                // all loads before the stores (as in the FP64 CG)
+                float *__restrict__ pv = a.p;
+                float *__restrict__ ev = a.e;
+                const float *__restrict__ rv = a.r;
+                const float *__restrict__ wv = a.w;
+#pragma unroll 4
                 for (int i = i0; i < re; i += kCgBlock) {
-                    const float po = a.p[i];
-                    a.e[i] = fmaf(alpha, po, a.e[i]);
-                    a.p[i] = fmaf(-delta, a.w[i], fmaf(beta, po, a.r[i]));
+                    const float po = pv[i], ei = ev[i], ri = rv[i], wi = wv[i];
+                    ev[i] = fmaf(alpha, po, ei);
+                    pv[i] = fmaf(-delta, wi, fmaf(beta, po, ri));
                 }
             }
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
@@ -582,12 +616,18 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             if (sc.refresh == 2) break;
             const float al = (float)sc.alpha;
             float rr32 = 0.0f, vr32 = 0.0f;
-#pragma unroll 2
-            for (int i = i0; i < re; i += kCgBlock) {
-                const float ri = fmaf(-al, a.q[i], a.r[i]);
-                a.r[i] = ri;
-                rr32 = fmaf(ri, ri, rr32);
-                vr32 = fmaf(a.v[i], ri, vr32);
+            {
+                float *__restrict__ rv = a.r;
+                const float *__restrict__ qv = a.q;
+                const float *__restrict__ vv = a.v;
+#pragma unroll 4
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const float qi = qv[i], rio = rv[i], vi = vv[i];
+                    const float ri = fmaf(-al, qi, rio);
+                    rv[i] = ri;
+                    rr32 = fmaf(ri, ri, rr32);
+                    vr32 = fmaf(vi, ri, vr32);
+                }
             }
             double v2[2] = {(double)rr32, (double)vr32};
             if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
