@@ -645,8 +645,10 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
             const double alpha = sc.alpha;
             double v3[1] = {0.0};
             for (int i = s0.lo + t0; i < s0.hi; i += step) {
-                a.x[i] += alpha * a.p[i];
-                const double ri = a.r[i] - alpha * a.q[i];
+                // all loads before the stores
+                const double xi = a.x[i], pi = a.p[i], rio = a.r[i], qi = a.q[i];
+                a.x[i] = xi + alpha * pi;
+                const double ri = rio - alpha * qi;
                 a.r[i] = ri;
                 seed0<V>(L0, i, ri);
                 v3[0] += ri * ri;

@@ -60,6 +60,10 @@ constexpr Sched kScheds[] = {{256, 2, 0, 1},  {256, 2, 1, 1},  {512, 1, 1, 1},  
                              {1024, 2, 1, 1}, {512, 2, 1, 2},  {1024, 2, 1, 2}, {512, 2, 1, 4},
                              {1024, 2, 1, 4}, {1024, 2, 1, 8}};
 constexpr int kNSched = sizeof(kScheds) / sizeof(kScheds[0]);
+// residual-norm rule of the CG (see krylov.cu): evaluate ||D^1/2 r^|| only
+// once min(D) r^.r^ is within kNearStop of thresh^2
+constexpr double kNearStop = 16.0;
+constexpr double kBoundMargin = 1.0 + 1e-8;
 
 // Block sum; result in tot[] (shared), visible to all threads on return.
 template <int BLOCK, int RED, int NV>
@@ -171,6 +175,36 @@ __device__ __forceinline__ void csum(double (&v)[NV], double *tot, double *cpart
     __syncthreads();
 }
 
+// Minimum over the cluster's blocks (every thread receives it).
+template <int BLOCK, int CL>
+__device__ __forceinline__ double cmin(double v)
+{
+    __shared__ double wmin[BLOCK / 32];
+    __shared__ double bmin;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = wmin[0];
+        for (int w = 1; w < BLOCK / 32; ++w) m = fmin(m, wmin[w]);
+        bmin = m;
+    }
+    if (CL > 1) {
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        cl.sync();
+        double m = bmin;
+        for (int r = 0; r < CL; ++r) m = fmin(m, *cl.map_shared_rank(&bmin, r));
+        cl.sync();                 // every block has read every block's bmin
+        __syncthreads();
+        if (threadIdx.x == 0) bmin = m;
+    }
+    __syncthreads();
+    const double r = bmin;
+    __syncthreads();
+    return r;
+}
+
 // next case for the cluster: rank 0 takes it from the queue
 template <int CL>
 __device__ __forceinline__ int cluster_next_case(int32_t *counter, int *slot)
@@ -204,8 +238,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
 {
     __shared__ int slot;
     __shared__ double tot[3], cpart[16];
-    __shared__ double sc_alpha, sc_beta, sc_rho, sc_thr, sc_nb, sc_nr0, sc_nr;
-    __shared__ int sc_phase;
+    __shared__ double sc_alpha, sc_beta, sc_rho, sc_thr, sc_nb, sc_nr0, sc_nr, sc_dmin;
+    __shared__ int sc_phase, sc_exact;
     const int rank = CL == 1 ? 0 : (int)cooperative_groups::this_cluster().block_rank();
     int par = 0;
     for (;;) {
@@ -217,11 +251,14 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
         const int r1 = a.start[cid] + min(n, (rank + 1) * chunk);
         const int i0 = r0 + threadIdx.x;
         int it = 0;
+        double dmin = INFINITY;
         for (int i = i0; i < r1; i += BLOCK) {
             const double d = a.diag[i], sq = sqrt(d);
             a.s[i] = 1.0 / sq;
             a.y[i] = a.x[i] * sq;
+            dmin = d > 0.0 ? fmin(dmin, d) : 0.0;
         }
+        dmin = cmin<BLOCK, CL>(dmin);     // (its cluster barriers also order s and y)
         csync<CL>();
         {
             double v3[3] = {0.0, 0.0, 0.0};
@@ -252,6 +289,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
             sc_thr = fmax(a.tol * sc_nb, a.reltol * sc_nr0);
             sc_alpha = sc_beta = 0.0;
             sc_phase = sc_nb == 0.0 ? 4 : (sc_nr0 <= sc_thr ? 1 : 0);
+            sc_dmin = dmin;
+            sc_exact = 1;
         }
         __syncthreads();
         if (sc_phase == 4) {
@@ -265,9 +304,10 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
                 } else {
 #pragma unroll U
                     for (int i = i0; i < r1; i += BLOCK) {
-                        const double po = a.p[i];
-                        a.y[i] += al * po;
-                        a.p[i] = a.r[i] + be * po;
+                        // all loads before the stores
+                        const double po = a.p[i], ri = a.r[i], yi = a.y[i];
+                        a.p[i] = ri + be * po;
+                        a.y[i] = yi + al * po;
                     }
                 }
                 csync<CL>();
@@ -292,23 +332,54 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_batch(BCg a)
                 }
                 __syncthreads();
                 if (sc_phase == 3) break;
+                // r^ -= alpha q and r^.r^; ||D^1/2 r^||^2 only once min(D) r^.r^
+                // allows the stop (the rule of the single-case CG: identical
+                // iterates and counts, two FP64 operations per row saved)
                 const double alpha = sc_alpha;
+                const bool exact = sc_exact || it >= a.maxit;
                 double v2[2] = {0.0, 0.0};
+                if (exact) {
+                    for (int i = i0; i < r1; i += BLOCK) {
+                        const double ri = a.r[i] - alpha * a.q[i];
+                        a.r[i] = ri;
+                        v2[0] += ri * ri;
+                        v2[1] += (a.diag[i] * ri) * ri;
+                    }
+                } else {
+                    double acc = 0.0;
 #pragma unroll U
-                for (int i = i0; i < r1; i += BLOCK) {
-                    const double ri = a.r[i] - alpha * a.q[i];
-                    a.r[i] = ri;
-                    const double r2 = ri * ri;
-                    v2[0] += r2;
-                    v2[1] += a.diag[i] * r2;
+                    for (int i = i0; i < r1; i += BLOCK) {
+                        const double qi = a.q[i], rio = a.r[i];
+                        const double ri = rio - alpha * qi;
+                        a.r[i] = ri;
+                        acc += ri * ri;
+                    }
+                    v2[0] = acc;
                 }
                 csum<BLOCK, RED, CL, 2>(v2, tot, cpart, par);
+                if (threadIdx.x == 0)
+                    sc_exact = exact ? 1 : (sc_dmin * tot[0] > sc_thr * sc_thr * kBoundMargin ? 0 : 2);
+                __syncthreads();
+                if (sc_exact == 2) {
+                    double v4[1] = {0.0};
+                    for (int i = i0; i < r1; i += BLOCK) {
+                        const double ri = a.r[i];
+                        v4[0] += (a.diag[i] * ri) * ri;
+                    }
+                    csum<BLOCK, RED, CL, 1>(v4, tot + 1, cpart, par);
+                }
                 if (threadIdx.x == 0) {
-                    sc_nr = sqrt(tot[1]);
-                    if (!isfinite(sc_nr)) sc_phase = 3;
-                    else if (sc_nr <= sc_thr) sc_phase = 1;
+                    const double rho = tot[0];
+                    const bool have = sc_exact != 0;
+                    sc_nr = have ? sqrt(tot[1]) : sqrt(sc_dmin * rho);
+                    if (!isfinite(sc_nr) || !isfinite(rho)) sc_phase = 3;
+                    else if (have && sc_nr <= sc_thr) sc_phase = 1;
                     else if (it >= a.maxit) sc_phase = 2;
-                    else { sc_beta = tot[0] / sc_rho; sc_rho = tot[0]; }
+                    else {
+                        sc_beta = rho / sc_rho;
+                        sc_rho = rho;
+                        sc_exact = sc_dmin * rho <= kNearStop * sc_thr * sc_thr ? 1 : 0;
+                    }
                 }
                 __syncthreads();
                 if (sc_phase != 0) break;
