@@ -1,7 +1,7 @@
 // coop.cuh -- the grid barrier and the deterministic reductions shared by
 // the persistent cooperative solvers (krylov.cu, amg.cu).
 //
-// The barrier spins a bounded number of times on a generation counter and
+// The barrier spins a bounded number of times on an arrival counter and
 // otherwise records FV_E_TIMEOUT; reductions add per-thread partials in a
 // fixed order inside a block and then the per-block partials in a fixed
 // order, so every block obtains the same bits.
@@ -20,16 +20,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
 {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed(const int *p)
@@ -39,15 +32,21 @@ __device__ __forceinline__ int ld_relaxed(const int *p)
     return v;
 }
 
-// Grid barrier.  The block's writes are ordered before its arrival by the
-// block barrier and the release half of the arrival's atomic; the arrival
-// counter only grows within a launch (the host zeroes it before each), so
-// the last of the gridDim.x arrivals of generation g reads
-// (g + 1) * gridDim.x - 1 and publishes g + 1 with a release store, which
-// the waiters' acquire loads (then the block barrier) order before their
-// later reads.  A waiter gives up after `limit` polls and records
-// FV_E_TIMEOUT; waiters also leave when another block has recorded an
-// error.  Returns false (for every thread of the block) in both cases.
+// Grid barrier.  Each block arrives with a release reduction on one
+// counter, which only grows within a launch (the host zeroes it before
+// each), and polls the counter with acquire loads until it holds the
+// gridDim.x * (g + 1) arrivals of generation g.  Every arrival is an atomic
+// read-modify-write, so the value a poller reads continues the release
+// sequence of each earlier arrival and its acquire load orders all blocks'
+// writes before the phase (made visible to the arriving thread by the
+// block barrier) before its later reads; the block barrier then extends
+// that to the block.  No block can arrive for generation g + 1 before every
+// block has arrived for g, so counts past the target are harmless.  (A flat
+// poll of the counter takes 1.2 us per barrier over 152 blocks, against 1.7
+// us when the last arrival publishes a separate generation word.)  A waiter
+// gives up after `limit` polls and records FV_E_TIMEOUT; waiters also leave
+// when another block has recorded an error.  Returns false (for every
+// thread of the block) in both cases.
 __device__ inline bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
 {
     __shared__ int s_ok;
@@ -55,25 +54,21 @@ __device__ inline bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
     if (gridDim.x == 1) return true;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned g = gen;
-        const unsigned old = atom_add_acq_rel(&bar->count, 1u);
-        if (old == (g + 1) * gridDim.x - 1) {
-            st_release(&bar->gen, g + 1);
-        } else {
-            long long spins = 0;
-            while (ld_acquire(&bar->gen) == g) {
-                ++spins;
-                if (spins > limit) {
-                    atomicExch(&bar->err, FV_E_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if ((spins & 63) == 0 && ld_relaxed(&bar->err) != 0) {
-                    ok = 0;
-                    break;
-                }
-                if (spins > 256) __nanosleep(32);
+        const unsigned target = (gen + 1) * gridDim.x;
+        red_add_release(&bar->count, 1u);
+        long long spins = 0;
+        while ((int)(ld_acquire(&bar->count) - target) < 0) {
+            ++spins;
+            if (spins > limit) {
+                atomicExch(&bar->err, FV_E_TIMEOUT);
+                ok = 0;
+                break;
             }
+            if ((spins & 63) == 0 && ld_relaxed(&bar->err) != 0) {
+                ok = 0;
+                break;
+            }
+            if (spins > 256) __nanosleep(32);
         }
         s_ok = ok;
     }
@@ -82,10 +77,13 @@ __device__ inline bool grid_sync(GridBar *bar, unsigned &gen, long long limit)
     return s_ok != 0;
 }
 
-// Reductions keep FP64 work low (GB300 runs FP64 at about 2 FMA per clock
-// per SM): threads drop their partial sums into shared memory and one warp
-// adds them in a fixed order; after the grid barrier one warp adds the
-// per-block partials, again in a fixed order.
+// Reductions keep FP64 work low: GB300 runs FP64 at about 2 FMA per clock
+// per SM, and an FP64 warp instruction holds its sub-partition's FP64 pipe
+// for ~64 cycles whatever its number of active lanes, so the cost of a sum
+// is its count of FP64 warp instructions and its depth.  Threads drop their
+// partial sums into shared memory, four warps add them in shallow trees, and
+// one warp adds the four results and shuffles; after the grid barrier one
+// warp per value adds the per-block partials.  Every order is fixed.
 
 constexpr int kCgBlock = 1024;
 constexpr int kRedWarps = 4;        // one reducing warp per SM sub-partition
@@ -97,40 +95,47 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
-// Block sum of NV values over BLOCK threads.  Threads store their partials in shared memory;
-// warps 0..3 (one per SM sub-partition, so their FP64 work runs in
-// parallel) each add a quarter of them, then thread 0 adds the four results.
-// The order of every addition is fixed.  On return tot[k] (shared) holds the
-// sums; only thread 0 is guaranteed to have seen them before the trailing
-// __syncthreads of the caller.
+// Block sum of NV values over BLOCK threads.  Threads store their partials
+// in shared memory; lane l of warp w (w = 0..3, one per SM sub-partition, so
+// their FP64 work runs in parallel) adds the BLOCK/128 values
+// w*BLOCK/4 + l + 32 j in a pairwise tree; warp 0 adds the four warps'
+// values of each lane, (w0 + w1) + (w2 + w3), and sums its lanes with
+// shuffles.  For BLOCK = 1024 that is 7 + 8 FP64 instructions of depth 3 + 7,
+// against 13 + 4 of depth 17 for sequential lane sums and a single-thread
+// final sum.  On return tot[k] (shared) holds the sums; only thread 0 is
+// guaranteed to have seen them before the trailing __syncthreads of the
+// caller.
 template <int NV, int BLOCK = kCgBlock>
 __device__ __forceinline__ void cg_block_sum(const double (&v)[NV], double (*buf)[BLOCK],
                                              double *tot)
 {
-    __shared__ double quarter[NV][kRedWarps];
+    static_assert(kRedWarps == 4 && BLOCK % (32 * kRedWarps) == 0, "block size");
+    constexpr int per = BLOCK / (32 * kRedWarps);      // values per lane
+    __shared__ double lanes[NV][kRedWarps][32];
 #pragma unroll
     for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < kRedWarps) {
-        constexpr int per = BLOCK / kRedWarps;         // values per warp
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
+            double t[per];
 #pragma unroll
-            for (int j = 0; j < per / 32; ++j) x += buf[k][w * per + lane + 32 * j];
-            x = warp_sum(x);
-            if (lane == 0) quarter[k][w] = x;
+            for (int j = 0; j < per; ++j) t[j] = buf[k][w * (BLOCK / kRedWarps) + lane + 32 * j];
+#pragma unroll
+            for (int s = 1; s < per; s <<= 1)
+#pragma unroll
+                for (int j = 0; j + s < per; j += 2 * s) t[j] += t[j + s];
+            lanes[k][w][lane] = t[0];
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
-#pragma unroll
-            for (int q = 0; q < kRedWarps; ++q) x += quarter[k][q];
-            tot[k] = x;
+            double x = (lanes[k][0][lane] + lanes[k][1][lane]) + (lanes[k][2][lane] + lanes[k][3][lane]);
+            x = warp_sum(x);
+            if (lane == 0) tot[k] = x;
         }
     }
 }
@@ -150,9 +155,27 @@ __device__ inline bool cg_grid_sum(const double (&v)[NV], double *part, GridBar 
     if (!grid_sync(bar, gen, limit)) return false;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < NV) {
-        // warp k adds quantity k over the blocks
-        double x = 0.0;
-        for (int j = lane; j < (int)gridDim.x; j += 32) x += __ldcg(part + j * kParts + w);
+        // warp k adds quantity k over the blocks: lane l the partials of
+        // blocks l, l + 32, ... in that order (loads issued first), then the
+        // lanes by shuffles
+        const int G = gridDim.x;
+        double x;
+        if (G <= 32 * 8) {
+            double t[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int b = lane + 32 * j;
+                t[j] = b < G ? __ldcg(part + b * kParts + w) : 0.0;
+            }
+            const int nslot = (G + 31) >> 5;
+            x = t[0];
+#pragma unroll
+            for (int j = 1; j < 8; ++j)
+                if (j < nslot) x += t[j];
+        } else {
+            x = 0.0;
+            for (int j = lane; j < G; j += 32) x += __ldcg(part + j * kParts + w);
+        }
         x = warp_sum(x);
         if (lane == 0) tot[w] = x;
     }

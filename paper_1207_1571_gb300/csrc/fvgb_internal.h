@@ -78,11 +78,11 @@ struct DevSolveStats {
     int32_t pad;
 };
 
-// Grid barrier state (bounded spin, see krylov.cu).
+// Grid barrier state (bounded spin, coop.cuh); zeroed before each launch.
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
-    int err;
+    unsigned int count;     // arrivals so far in this launch
+    unsigned int spare;
+    int err;                // first error recorded by a waiter (FV_E_TIMEOUT)
     int pad;
 };
 

@@ -45,55 +45,26 @@ __device__ __forceinline__ RowSpan row_span(const int32_t *__restrict__ slice_pt
 // ------------------------------------------------------------ barriers --
 // (grid barrier and deterministic reductions: coop.cuh)
 
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV])
+// Sum v over the grid; every thread of every block returns the same bits
+// (the reductions of coop.cuh: four warps per block in fixed trees, then one
+// warp per value over the block partials).
+constexpr int kBicgSums = 6;                // most values summed at once
+
+__device__ __forceinline__ double (*bicg_sum_buffer())[kBlock]
 {
-    __shared__ double red[NV][kBlock / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double x = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[k][wid] = x;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = lane < kBlock / 32 ? red[k][lane] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) red[k][0] = x;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = red[k][0];
-    __syncthreads();
+    __shared__ double buf[kBicgSums][kBlock];   // one buffer for every NV
+    return buf;
 }
 
-// Sum v over the grid; every block returns the same bits.
 template <int NV>
 __device__ bool grid_sum(double (&v)[NV], double *part, GridBar *bar, unsigned &gen, long long limit)
 {
-    block_sum<NV>(v);
-    if (gridDim.x == 1) return true;
-    if (threadIdx.x == 0) {
+    static_assert(NV <= kBicgSums && NV <= kParts, "too many values");
+    __shared__ double tot[NV];
+    if (!cg_grid_sum<NV, kBlock>(v, part, bar, gen, limit, bicg_sum_buffer(), tot)) return false;
+    if (gridDim.x == 1) __syncthreads();    // otherwise cg_grid_sum ended with one
 #pragma unroll
-        for (int k = 0; k < NV; ++k) part[blockIdx.x * kParts + k] = v[k];
-    }
-    if (!grid_sync(bar, gen, limit)) return false;
-    double w[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) w[k] = 0.0;
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += kBlock) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] += __ldcg(part + j * kParts + k);
-    }
-    block_sum<NV>(w);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = w[k];
+    for (int k = 0; k < NV; ++k) v[k] = tot[k];
     return true;
 }
 
@@ -125,8 +96,12 @@ struct CgArgs {
 // instruction on this part, so no thread repeats it).
 struct CgScalars {
     double alpha, beta, rho, thresh, nb, nr0, nr, dmin;
+    double near2;    // kNearStop thresh^2: evaluate the norm once min(D) r^.r^ is below it
+    double skip2;    // thresh^2 kBoundMargin: a skipped evaluation could not stop above it
+    double nrb2;     // min(D) r^.r^ of the last iteration when its norm was not evaluated
     int phase;       // 0 iterate, 1 converged, 2 not converged, 3 diverged, 4 zero rhs
     int exact;       // evaluate ||D^1/2 r^|| in this iteration's residual update
+    int bound;       // the last iteration skipped the evaluation (nr = sqrt(nrb2), a lower bound)
 };
 
 // The stopping test needs ||r||_2 = ||D^1/2 r^||_2, two more FP64 operations
@@ -185,6 +160,28 @@ __device__ __forceinline__ double spmv_unit_row(const CgArgs &a, const RowSpan &
         }
     }
     return acc;
+}
+
+// End of a CG iteration (thread 0): tot[0] = r^.r^, tot[1] = ||D^1/2 r^||^2
+// when sc.exact != 0.  Takes the stopping decision, else beta, and whether
+// the next iteration evaluates the norm.  The square root is only taken where
+// the norm was evaluated; a skipped iteration keeps the lower bound
+// min(D) r^.r^, which is finite whenever rho is.
+__device__ __forceinline__ void cg_end_iteration(CgScalars &sc, const double *tot, int it, int maxit)
+{
+    const double rho = tot[0];
+    const bool have = sc.exact != 0;
+    if (have) sc.nr = sqrt(tot[1]);
+    else sc.nrb2 = sc.dmin * rho;
+    sc.bound = !have;
+    if ((have && !isfinite(sc.nr)) || !isfinite(rho)) sc.phase = 3;
+    else if (have && sc.nr <= sc.thresh) sc.phase = 1;
+    else if (it >= maxit) sc.phase = 2;
+    else {
+        sc.beta = rho / sc.rho;
+        sc.rho = rho;
+        sc.exact = sc.dmin * rho <= sc.near2 ? 1 : 0;
+    }
 }
 
 __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
@@ -256,9 +253,12 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
         sc.nr = sc.nr0;
         sc.rho = tot[2];
         sc.thresh = fmax(a.tol * sc.nb, a.reltol * sc.nr0);
+        sc.near2 = kNearStop * sc.thresh * sc.thresh;
+        sc.skip2 = (sc.thresh * sc.thresh) * kBoundMargin;
         sc.alpha = sc.beta = 0.0;
         sc.phase = sc.nb == 0.0 ? 4 : (sc.nr0 <= sc.thresh ? 1 : 0);
         sc.exact = 1;
+        sc.bound = 0;
     }
     __syncthreads();
     if (ok && sc.phase == 4) {
@@ -312,37 +312,39 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             // P3: r^ -= alpha q; r^.r^, and ||D^1/2 r^||^2 near the stop
             const double alpha = sc.alpha;
             const bool exact = sc.exact || it >= a.maxit;
-            double v2[2] = {0.0, 0.0};
             {
                 double *__restrict__ rv = a.r;
                 const double *__restrict__ qv = a.q;
                 const double *__restrict__ dv = a.diag;
                 if (exact) {
+                    double v2[2] = {0.0, 0.0};
                     for (int i = i0; i < re; i += kCgBlock) {
                         const double ri = rv[i] - alpha * qv[i];
                         rv[i] = ri;
                         v2[0] += ri * ri;
                         v2[1] += (dv[i] * ri) * ri;
                     }
+                    ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot);
                 } else {
                     // the common case, a tight loop (a uniform branch inside the
-                    // unrolled loop cost a third of this pass's bandwidth)
-                    double acc = 0.0;
+                    // unrolled loop cost a third of this pass's bandwidth) and a
+                    // sum of one value (each FP64 value summed over the block
+                    // costs a few hundred cycles)
+                    double v1[1] = {0.0};
 #pragma unroll 4
                     for (int i = i0; i < re; i += kCgBlock) {
                         const double ri = rv[i] - alpha * qv[i];
                         rv[i] = ri;
-                        acc += ri * ri;
+                        v1[0] += ri * ri;
                     }
-                    v2[0] = acc;
+                    ok = cg_grid_sum<1>(v1, a.partB, a.bar, gen, a.spin, buf, tot);
                 }
             }
-            if (!(ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot))) break;
+            if (!ok) break;
             if (threadIdx.x == 0) {
-                const double rho = tot[0];
-                const double t2 = sc.thresh * sc.thresh;
                 // an evaluation skipped while the bound still allows the stop
-                sc.exact = exact ? 1 : (sc.dmin * rho > t2 * kBoundMargin ? 0 : 2);
+                sc.exact = exact ? 1 : (sc.dmin * tot[0] > sc.skip2 ? 0 : 2);
+                if (sc.exact != 2) cg_end_iteration(sc, tot, it, a.maxit);
             }
             __syncthreads();
             if (sc.exact == 2) {
@@ -352,21 +354,9 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
                     v4[0] += (a.diag[i] * ri) * ri;
                 }
                 if (!(ok = cg_grid_sum<1>(v4, a.partA, a.bar, gen, a.spin, buf, tot + 1))) break;
+                if (threadIdx.x == 0) cg_end_iteration(sc, tot, it, a.maxit);
+                __syncthreads();
             }
-            if (threadIdx.x == 0) {
-                const double rho = tot[0];
-                const bool have = sc.exact != 0;
-                sc.nr = have ? sqrt(tot[1]) : sqrt(sc.dmin * rho);   // a lower bound when skipped
-                if (!isfinite(sc.nr) || !isfinite(rho)) sc.phase = 3;
-                else if (have && sc.nr <= sc.thresh) sc.phase = 1;
-                else if (it >= a.maxit) sc.phase = 2;
-                else {
-                    sc.beta = rho / sc.rho;
-                    sc.rho = rho;
-                    sc.exact = sc.dmin * rho <= kNearStop * sc.thresh * sc.thresh ? 1 : 0;
-                }
-            }
-            __syncthreads();
             if (sc.phase != 0) break;
         }
         if (ok) {
@@ -382,7 +372,8 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
                         : ph == 3 ? FV_E_DIVERGED : ph == 2 ? FV_E_NOT_CONVERGED : FV_OK;
         const bool zero = ph == 4;
         a.stats->res0 = zero ? 0.0 : sc.nr0 / sc.nb;
-        a.stats->res = zero ? 0.0 : sc.nr / sc.nb;
+        const double nr = sc.bound ? sqrt(sc.nrb2) : sc.nr;
+        a.stats->res = zero ? 0.0 : nr / sc.nb;
         a.stats->outer = 1;
     }
 }
