@@ -91,33 +91,46 @@ __device__ __forceinline__ void bsum(double (&v)[NV], double *tot)
             }
         }
     } else {
-        // stage in shared memory; warps 0..NR-1 add one slice each
+        // stage in shared memory; lane l of warp w < NR adds the values
+        // w*BLOCK/NR + l + 32 j in a pairwise tree, warp 0 adds the NR
+        // results of each lane and shuffles (the cost of a sum on this
+        // FP64-bound kernel is its count of FP64 warp instructions: 3 + 8
+        // for 512 threads, against 4 + 5 per warp and 4 on thread 0)
         constexpr int NR = W < 4 ? W : 4;
+        constexpr int per = BLOCK / (32 * NR);
         __shared__ double stg[NV][BLOCK];
-        __shared__ double part[NV][NR];
+        __shared__ double lanes[NV][NR][32];
 #pragma unroll
         for (int k = 0; k < NV; ++k) stg[k][threadIdx.x] = v[k];
         __syncthreads();
         if (w < NR) {
-            constexpr int per = BLOCK / NR;
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                double x = 0.0;
+                double t[per];
 #pragma unroll
-                for (int j = 0; j < per / 32; ++j) x += stg[k][w * per + lane + 32 * j];
+                for (int j = 0; j < per; ++j) t[j] = stg[k][w * (BLOCK / NR) + lane + 32 * j];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0) part[k][w] = x;
+                for (int st = 1; st < per; st <<= 1)
+#pragma unroll
+                    for (int j = 0; j + st < per; j += 2 * st) t[j] += t[j + st];
+                lanes[k][w][lane] = t[0];
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (w == 0) {
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                double x = 0.0;
+                double x;
+                if (NR == 4) {
+                    x = (lanes[k][0][lane] + lanes[k][1][lane]) + (lanes[k][2][lane] + lanes[k][3][lane]);
+                } else {
+                    x = lanes[k][0][lane];
 #pragma unroll
-                for (int q = 0; q < NR; ++q) x += part[k][q];
-                tot[k] = x;
+                    for (int q = 1; q < NR; ++q) x += lanes[k][q][lane];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) tot[k] = x;
             }
         }
     }
@@ -167,8 +180,8 @@ __device__ __forceinline__ void csum(double (&v)[NV], double *tot, double *cpart
     if (threadIdx.x < NV) cpart[par * 8 + threadIdx.x] = tot[threadIdx.x];
     cl.sync();
     if (threadIdx.x < NV) {
-        double x = 0.0;
-        for (int r = 0; r < CL; ++r) x += cl.map_shared_rank(cpart, r)[par * 8 + threadIdx.x];
+        double x = cl.map_shared_rank(cpart, 0)[par * 8 + threadIdx.x];
+        for (int r = 1; r < CL; ++r) x += cl.map_shared_rank(cpart, r)[par * 8 + threadIdx.x];
         tot[threadIdx.x] = x;
     }
     par ^= 1;    // the next reduction uses the other half (see the barrier argument above)
