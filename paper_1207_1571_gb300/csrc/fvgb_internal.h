@@ -91,6 +91,7 @@ struct KrylovWork {
     int G = 0;               // cooperative grid size of the BiCGStab kernel
     int Gcg = 0;             // cooperative grid size of the CG kernel (one block per SM)
     int block = 0;
+    int cg_res_max = 0;      // dynamic shared memory the resident CG form may use (bytes)
     double *val = nullptr;   // SELL values (scaled copy for CG)
     double *val2 = nullptr;  // second SELL value buffer (BiCGStab input copy)
     double *dinv = nullptr;  // [N] (BiCGStab) / scaling s (CG)

@@ -23,6 +23,8 @@
 // unscaled method does.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+
 #include "fvgb_internal.h"
 #include "coop.cuh"
 
@@ -184,17 +186,36 @@ __device__ __forceinline__ void cg_end_iteration(CgScalars &sc, const double *to
     }
 }
 
+// Rows of block b: [b chunk, min(N, (b + 1) chunk)), whole 32-row slices.
+__host__ __device__ __forceinline__ int cg_chunk(int N, int G)
+{
+    const int nsl = (N + 31) >> 5;
+    return ((nsl + G - 1) / G) * 32;
+}
+
+// RES: the row-local vectors r^, q and y (each read and written only by the
+// thread that owns the row) live in the block's shared memory, 3 x chunk
+// doubles of dynamic shared memory; only p (gathered by neighbouring rows)
+// and the matrix go through L2 and HBM.  On the 1M-cell cavity a block owns
+// 6592 rows: 158 KB of the 227 KB a block may hold.  Otherwise the vectors
+// are the workspace arrays in global memory.  Both forms do the same
+// arithmetic in the same order.
+template <bool RES>
 __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
 {
     __shared__ double buf[3][kCgBlock];
     __shared__ double tot[3];
     __shared__ CgScalars sc;
+    extern __shared__ double resv[];
     const int N = a.N;
-    const int nsl = (N + 31) >> 5;
-    const int chunk = ((nsl + gridDim.x - 1) / gridDim.x) * 32;
+    const int chunk = cg_chunk(N, gridDim.x);
     const int rb = blockIdx.x * chunk;
-    const int re = min(N, rb + chunk);
-    const int i0 = rb + threadIdx.x;
+    const int nl = min(N, rb + chunk) - rb;      // rows of this block (none if <= 0)
+    const int t0 = threadIdx.x;
+    // own-row views, indexed by the row's offset in the block
+    double *const rl = RES ? resv : a.r + rb;
+    double *const ql = RES ? resv + chunk : a.q + rb;
+    double *const yl = RES ? resv + 2 * chunk : a.y + rb;
     unsigned gen = 0;
     bool ok = true;
     int it = 0;
@@ -203,11 +224,12 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
     // smallest diagonal (0 if any is not positive) in its partial record
     {
         double dmin = INFINITY;
-        for (int i = i0; i < re; i += kCgBlock) {
+        for (int l = t0; l < nl; l += kCgBlock) {
+            const int i = rb + l;
             const double d = a.diag[i];
             const double sq = sqrt(d);
             a.s[i] = 1.0 / sq;
-            a.y[i] = a.x[i] * sq;
+            yl[l] = a.x[i] * sq;
             dmin = d > 0.0 ? fmin(dmin, d) : 0.0;
         }
         dmin = block_min(dmin);
@@ -217,7 +239,8 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
     // S2: scale the off-diagonals, r^ = s (b - A x), norms
     if (ok) {
         double v3[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||r||^2, r^.r^
-        for (int i = i0; i < re; i += kCgBlock) {
+        for (int l = t0; l < nl; l += kCgBlock) {
+            const int i = rb + l;
             const RowSpan rs = row_span(a.slice_ptr, i);
             const double si = a.s[i], d = a.diag[i], xi = a.x[i];
             double ax = d * xi;
@@ -230,7 +253,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             }
             const double bi = a.b[i];
             const double rh = si * (bi - ax);
-            a.r[i] = rh;
+            rl[l] = rh;
             v3[0] += bi * bi;
             v3[1] += d * rh * rh;
             v3[2] += rh * rh;
@@ -262,42 +285,44 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
     }
     __syncthreads();
     if (ok && sc.phase == 4) {
-        for (int i = i0; i < re; i += kCgBlock) a.x[i] = 0.0;
+        for (int l = t0; l < nl; l += kCgBlock) a.x[rb + l] = 0.0;
     } else if (ok && sc.phase == 0) {
+        double *const pl = a.p + rb;
         while (true) {
             ++it;
             // P1: p = r^ + beta p (first: p = r^); y += alpha_prev p_prev
             if (it == 1) {
-                for (int i = i0; i < re; i += kCgBlock) a.p[i] = a.r[i];
+                for (int l = t0; l < nl; l += kCgBlock) pl[l] = rl[l];
             } else {
                 // restrict-qualified copies and all three loads before the
                 // two stores: several rows' loads stay in flight at once
                 // (with y += alpha p written as a load-modify-store first,
                 // this pass ran at 62 % of the copy bandwidth instead of 80 %)
                 const double alpha = sc.alpha, beta = sc.beta;
-                double *__restrict__ yv = a.y;
-                double *__restrict__ pv = a.p;
-                const double *__restrict__ rv = a.r;
+                double *__restrict__ yv = yl;
+                double *__restrict__ pv = pl;
+                const double *__restrict__ rv = rl;
 #pragma unroll 4
-                for (int i = i0; i < re; i += kCgBlock) {
-                    const double po = pv[i];
-                    const double ri = rv[i];
-                    const double yi = yv[i];
-                    pv[i] = ri + beta * po;
-                    yv[i] = yi + alpha * po;
+                for (int l = t0; l < nl; l += kCgBlock) {
+                    const double po = pv[l];
+                    const double ri = rv[l];
+                    const double yi = yv[l];
+                    pv[l] = ri + beta * po;
+                    yv[l] = yi + alpha * po;
                 }
             }
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
             // P2: q = A^ p (unit diagonal), p.q
             double v1[1] = {0.0};
             {
-                double *__restrict__ qv = a.q;
+                double *__restrict__ qv = ql;
 #pragma unroll 2
-                for (int i = i0; i < re; i += kCgBlock) {
+                for (int l = t0; l < nl; l += kCgBlock) {
+                    const int i = rb + l;
                     const RowSpan rs = row_span(a.slice_ptr, i);
                     const double pi = a.p[i];
                     const double acc = spmv_unit_row(a, rs, pi);
-                    qv[i] = acc;
+                    qv[l] = acc;
                     v1[0] += pi * acc;
                 }
             }
@@ -313,16 +338,16 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             const double alpha = sc.alpha;
             const bool exact = sc.exact || it >= a.maxit;
             {
-                double *__restrict__ rv = a.r;
-                const double *__restrict__ qv = a.q;
-                const double *__restrict__ dv = a.diag;
+                double *__restrict__ rv = rl;
+                const double *__restrict__ qv = ql;
+                const double *__restrict__ dv = a.diag + rb;
                 if (exact) {
                     double v2[2] = {0.0, 0.0};
-                    for (int i = i0; i < re; i += kCgBlock) {
-                        const double ri = rv[i] - alpha * qv[i];
-                        rv[i] = ri;
+                    for (int l = t0; l < nl; l += kCgBlock) {
+                        const double ri = rv[l] - alpha * qv[l];
+                        rv[l] = ri;
                         v2[0] += ri * ri;
-                        v2[1] += (dv[i] * ri) * ri;
+                        v2[1] += (dv[l] * ri) * ri;
                     }
                     ok = cg_grid_sum<2>(v2, a.partB, a.bar, gen, a.spin, buf, tot);
                 } else {
@@ -332,9 +357,9 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
                     // costs a few hundred cycles)
                     double v1[1] = {0.0};
 #pragma unroll 4
-                    for (int i = i0; i < re; i += kCgBlock) {
-                        const double ri = rv[i] - alpha * qv[i];
-                        rv[i] = ri;
+                    for (int l = t0; l < nl; l += kCgBlock) {
+                        const double ri = rv[l] - alpha * qv[l];
+                        rv[l] = ri;
                         v1[0] += ri * ri;
                     }
                     ok = cg_grid_sum<1>(v1, a.partB, a.bar, gen, a.spin, buf, tot);
@@ -349,9 +374,9 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
             __syncthreads();
             if (sc.exact == 2) {
                 double v4[1] = {0.0};
-                for (int i = i0; i < re; i += kCgBlock) {
-                    const double ri = a.r[i];
-                    v4[0] += (a.diag[i] * ri) * ri;
+                for (int l = t0; l < nl; l += kCgBlock) {
+                    const double ri = rl[l];
+                    v4[0] += (a.diag[rb + l] * ri) * ri;
                 }
                 if (!(ok = cg_grid_sum<1>(v4, a.partA, a.bar, gen, a.spin, buf, tot + 1))) break;
                 if (threadIdx.x == 0) cg_end_iteration(sc, tot, it, a.maxit);
@@ -362,7 +387,10 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg(CgArgs a)
         if (ok) {
             // final update of the scaled iterate, then x = D^-1/2 y
             const double af = (sc.phase == 3) ? 0.0 : sc.alpha;
-            for (int i = i0; i < re; i += kCgBlock) a.x[i] = a.s[i] * (a.y[i] + af * a.p[i]);
+            for (int l = t0; l < nl; l += kCgBlock) {
+                const int i = rb + l;
+                a.x[i] = a.s[i] * (yl[l] + af * a.p[i]);
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -840,12 +868,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
 
 // ------------------------------------------------------------ launches --
 
-static fv_status coop_launch(const void *fn, int G, int block, void **args, cudaStream_t s)
+static fv_status coop_launch(const void *fn, int G, int block, void **args, cudaStream_t s,
+                             size_t smem = 0)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -865,12 +894,43 @@ static int grid_for(int rows, int block, int gmax)
     return want < gmax ? want : gmax;
 }
 
+// The CG launch: the resident form when the block's r^, q and y fit in the
+// dynamic shared memory krylov_setup allowed, else the global form.
+static fv_status launch_k_pcg(const fv_mesh *m, int G, CgArgs &a)
+{
+    void *args[] = {&a};
+    const size_t res = (size_t)3 * sizeof(double) * cg_chunk(m->N, G);
+    if (res <= (size_t)m->kw.cg_res_max)
+        return coop_launch((const void *)k_pcg<true>, G, kCgBlock, args, m->stream, res);
+    return coop_launch((const void *)k_pcg<false>, G, kCgBlock, args, m->stream);
+}
+
 fv_status krylov_setup(fv_mesh *m)
 {
     KrylovWork &w = m->kw;
     int per_sm = 0;
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kCgBlock, 0));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<false>, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "CG kernel cannot be resident");
+    {
+        // the resident CG form may take what a block can hold beyond its
+        // static shared memory, if one block per SM stays co-resident
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        FV_CUDA(cudaGetDevice(&dev));
+        FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        FV_CUDA(cudaFuncGetAttributes(&fa, k_pcg<true>));
+        const int room = optin - (int)fa.sharedSizeBytes;
+        w.cg_res_max = 0;
+        if (room > 0) {
+            FV_CUDA(cudaFuncSetAttribute(k_pcg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, room));
+            int per = 0;
+            FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<true>, kCgBlock, room));
+            if (per >= 1) w.cg_res_max = room;
+        }
+        // FVGB_CG_RESIDENT=0 keeps the global form (tests compare the two)
+        if (const char *env = std::getenv("FVGB_CG_RESIDENT"))
+            if (std::atoi(env) == 0) w.cg_res_max = 0;
+    }
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel cannot be resident");
     w.Gcg = m->sm_count;
@@ -925,9 +985,7 @@ fv_status launch_pcg(const fv_mesh *m, const CgProblem &pb)
     a.maxit = pb.maxit;
     a.stats = pb.stats;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
-    void *args[] = {&a};
-    return coop_launch((const void *)k_pcg, grid_for(m->N, kCgBlock, w.Gcg), kCgBlock, args,
-                       m->stream);
+    return launch_k_pcg(m, grid_for(m->N, kCgBlock, w.Gcg), a);
 }
 
 fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb)
@@ -1004,8 +1062,7 @@ fv_status launch_pcg_scratch(const fv_mesh *m, const CgProblem &pb, const CgScra
     FV_CHECK(G <= ws.max_blocks, FV_E_INVALID, "scratch holds partial sums for %d blocks, %d needed",
              ws.max_blocks, G);
     FV_CUDA(cudaMemsetAsync(ws.bar, 0, sizeof(GridBar), m->stream));
-    void *args[] = {&a};
-    return coop_launch((const void *)k_pcg, G, kCgBlock, args, m->stream);
+    return launch_k_pcg(m, G, a);
 }
 
 fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)

@@ -362,6 +362,29 @@ def test_graph_replay_and_determinism(P):
     assert sb["status"] == 0
 
 
+def test_cg_resident_and_global_forms_identical(P, monkeypatch):
+    """The CG keeps r^, q and y in shared memory when a block's rows fit
+    (meshes up to about 1.2M cells on GB300) and in global memory otherwise;
+    both forms do the same arithmetic in the same order, so a mesh created
+    with FVGB_CG_RESIDENT=0 (global form only) gives the same bits."""
+    m = mg.permute_cells(mg.cavity3d(24), mg.random_permutation(24 ** 3, 5))
+    out = []
+    for env in ("1", "0"):
+        monkeypatch.setenv("FVGB_CG_RESIDENT", env)
+        mesh = P.Mesh(m, renumber=True)
+        case = P.Case(mesh, 0.01)
+        its = []
+        for _ in range(3):
+            s = case.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
+            assert s["status"] == 0
+            its.append([int(k) for k in s["iters"]])
+        out.append((case.get_fields_host(), its))
+    (fa, ia), (fb, ib) = out
+    assert ia == ib
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+
+
 def test_fields_roundtrip(P):
     m = mg.permute_cells(mg.cavity3d(5), mg.random_permutation(125, 9))
     mesh = P.Mesh(m, renumber=True)
