@@ -92,6 +92,7 @@ struct KrylovWork {
     int Gcg = 0;             // cooperative grid size of the CG kernel (one block per SM)
     int block = 0;
     int cg_res_max = 0;      // dynamic shared memory the resident CG form may use (bytes)
+    int mix_res_max = 0;     // the same for the resident mixed-precision CG form
     double *val = nullptr;   // SELL values (scaled copy for CG)
     double *val2 = nullptr;  // second SELL value buffer (BiCGStab input copy)
     double *dinv = nullptr;  // [N] (BiCGStab) / scaling s (CG)

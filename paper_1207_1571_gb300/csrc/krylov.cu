@@ -479,6 +479,12 @@ __device__ __forceinline__ float spmv32_unit_row(const MixArgs &a, const RowSpan
     return acc;
 }
 
+// RES: the row-local FP32 vectors r^, q, e, w and v (each read and written
+// only by the thread that owns the row) live in the block's shared memory,
+// 5 x chunk floats of dynamic shared memory; p (gathered by neighbouring
+// rows), the matrices and the FP64 vectors stay in global memory.  Both forms
+// do the same arithmetic in the same order.
+template <bool RES>
 __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
 {
     __shared__ double buf[3][kCgBlock];
@@ -490,6 +496,15 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
     const int rb = blockIdx.x * chunk;
     const int re = min(N, rb + chunk);
     const int i0 = rb + threadIdx.x;
+    extern __shared__ float resf[];
+    // the FP32 row vectors, indexed by i - o: shared (offset by the block's
+    // first row) or global
+    const int o = RES ? rb : 0;
+    float *const rl = RES ? resf : a.r;
+    float *const ql = RES ? resf + chunk : a.q;
+    float *const el = RES ? resf + 2 * chunk : a.e;
+    float *const wl = RES ? resf + 3 * chunk : a.w;
+    float *const vl = RES ? resf + 4 * chunk : a.v;
     unsigned gen = 0;
     bool ok = true;
     int it = 0, outer = 0;
@@ -511,8 +526,8 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
                 a.val32[e] = (float)(v * si * a.s[a.col[e]]);
             }
             a.a1[i] = row;
-            a.w[i] = (float)(1.0 / si);
-            a.v[i] = (float)(si * row);
+            wl[i - o] = (float)(1.0 / si);
+            vl[i - o] = (float)(si * row);
             v1[0] += row;
         }
         ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf, tot);
@@ -558,11 +573,11 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
                 const double ri = a.r64[i] - sh * a.a1[i];
                 a.x[i] += sh;
                 const float rh = (float)(a.s[i] * ri);
-                a.r[i] = rh;
-                a.e[i] = 0.0f;
+                rl[i - o] = rh;
+                el[i - o] = 0.0f;
                 v3[0] += ri * ri;
                 v3[1] += (double)rh * (double)rh;
-                v3[2] += (double)a.v[i] * (double)rh;
+                v3[2] += (double)vl[i - o] * (double)rh;
             }
             if (!(ok = cg_grid_sum<3>(v3, a.partA, a.bar, gen, a.spin, buf, tot))) break;
         }
@@ -599,17 +614,17 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             ++it;
             const float alpha = (float)sc.alpha, beta = (float)sc.beta, delta = (float)sc.delta;
             if (sc.restart) {
-                for (int i = i0; i < re; i += kCgBlock) a.p[i] = fmaf(-delta, a.w[i], a.r[i]);
+                for (int i = i0; i < re; i += kCgBlock) a.p[i] = fmaf(-delta, wl[i - o], rl[i - o]);
             } else {
                 // all loads before the stores (as in the FP64 CG)
                 float *__restrict__ pv = a.p;
-                float *__restrict__ ev = a.e;
-                const float *__restrict__ rv = a.r;
-                const float *__restrict__ wv = a.w;
+                float *__restrict__ ev = el;
+                const float *__restrict__ rv = rl;
+                const float *__restrict__ wv = wl;
 #pragma unroll 4
                 for (int i = i0; i < re; i += kCgBlock) {
-                    const float po = pv[i], ei = ev[i], ri = rv[i], wi = wv[i];
-                    ev[i] = fmaf(alpha, po, ei);
+                    const float po = pv[i], ei = ev[i - o], ri = rv[i - o], wi = wv[i - o];
+                    ev[i - o] = fmaf(alpha, po, ei);
                     pv[i] = fmaf(-delta, wi, fmaf(beta, po, ri));
                 }
             }
@@ -620,7 +635,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
                 const RowSpan rs = row_span(a.slice_ptr, i);
                 const float pi = a.p[i];
                 const float acc = spmv32_unit_row(a, rs, pi);
-                a.q[i] = acc;
+                ql[i - o] = acc;
                 pq32 = fmaf(pi, acc, pq32);
             }
             double v1[1] = {(double)pq32};
@@ -636,14 +651,14 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             const float al = (float)sc.alpha;
             float rr32 = 0.0f, vr32 = 0.0f;
             {
-                float *__restrict__ rv = a.r;
-                const float *__restrict__ qv = a.q;
-                const float *__restrict__ vv = a.v;
+                float *__restrict__ rv = rl;
+                const float *__restrict__ qv = ql;
+                const float *__restrict__ vv = vl;
 #pragma unroll 4
                 for (int i = i0; i < re; i += kCgBlock) {
-                    const float qi = qv[i], rio = rv[i], vi = vv[i];
+                    const float qi = qv[i - o], rio = rv[i - o], vi = vv[i - o];
                     const float ri = fmaf(-al, qi, rio);
-                    rv[i] = ri;
+                    rv[i - o] = ri;
                     rr32 = fmaf(ri, ri, rr32);
                     vr32 = fmaf(vi, ri, vr32);
                 }
@@ -672,7 +687,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
         {
             const float al = (float)sc.alpha;
             for (int i = i0; i < re; i += kCgBlock) {
-                const float ei = fmaf(al, a.p[i], a.e[i]);
+                const float ei = fmaf(al, a.p[i], el[i - o]);
                 a.x[i] += a.s[i] * (double)ei;
             }
         }
@@ -905,33 +920,43 @@ static fv_status launch_k_pcg(const fv_mesh *m, int G, CgArgs &a)
     return coop_launch((const void *)k_pcg<false>, G, kCgBlock, args, m->stream);
 }
 
+// Dynamic shared memory a resident form may use: what a block can hold beyond
+// the kernel's static shared memory, provided one block per SM stays resident
+// with it (0: use the global form).
+static fv_status resident_room(const void *fn, bool allow, int *out)
+{
+    *out = 0;
+    if (!allow) return FV_OK;
+    int dev = 0, optin = 0, per = 0;
+    cudaFuncAttributes fa;
+    FV_CUDA(cudaGetDevice(&dev));
+    FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    FV_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const int room = optin - (int)fa.sharedSizeBytes;
+    if (room <= 0) return FV_OK;
+    FV_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, room));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCgBlock, room));
+    if (per >= 1) *out = room;
+    return FV_OK;
+}
+
 fv_status krylov_setup(fv_mesh *m)
 {
     KrylovWork &w = m->kw;
     int per_sm = 0;
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<false>, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "CG kernel cannot be resident");
+    // the resident CG forms may take what a block can hold beyond its static
+    // shared memory, if one block per SM stays co-resident;
+    // FVGB_CG_RESIDENT=0 keeps the global forms (tests compare the two)
     {
-        // the resident CG form may take what a block can hold beyond its
-        // static shared memory, if one block per SM stays co-resident
-        int dev = 0, optin = 0;
-        cudaFuncAttributes fa;
-        FV_CUDA(cudaGetDevice(&dev));
-        FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        FV_CUDA(cudaFuncGetAttributes(&fa, k_pcg<true>));
-        const int room = optin - (int)fa.sharedSizeBytes;
-        w.cg_res_max = 0;
-        if (room > 0) {
-            FV_CUDA(cudaFuncSetAttribute(k_pcg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, room));
-            int per = 0;
-            FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<true>, kCgBlock, room));
-            if (per >= 1) w.cg_res_max = room;
-        }
-        // FVGB_CG_RESIDENT=0 keeps the global form (tests compare the two)
-        if (const char *env = std::getenv("FVGB_CG_RESIDENT"))
-            if (std::atoi(env) == 0) w.cg_res_max = 0;
+        const char *env = std::getenv("FVGB_CG_RESIDENT");
+        const bool allow = !(env && std::atoi(env) == 0);
+        fv_status st;
+        if ((st = resident_room((const void *)k_pcg<true>, allow, &w.cg_res_max)) != FV_OK) return st;
+        if ((st = resident_room((const void *)k_pcg_mixed<true>, allow, &w.mix_res_max)) != FV_OK) return st;
     }
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed, kCgBlock, 0));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed<false>, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel cannot be resident");
     w.Gcg = m->sm_count;
     int per_sm2 = 0;
@@ -1029,8 +1054,11 @@ fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb)
     a.stats = pb.stats;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
     void *args[] = {&a};
-    return coop_launch((const void *)k_pcg_mixed, grid_for(m->N, kCgBlock, w.Gcg), kCgBlock, args,
-                       m->stream);
+    const int G = grid_for(m->N, kCgBlock, w.Gcg);
+    const size_t res = (size_t)5 * sizeof(float) * cg_chunk(m->N, G);
+    if (res <= (size_t)w.mix_res_max)
+        return coop_launch((const void *)k_pcg_mixed<true>, G, kCgBlock, args, m->stream, res);
+    return coop_launch((const void *)k_pcg_mixed<false>, G, kCgBlock, args, m->stream);
 }
 
 // Same CG launch with caller-supplied work vectors (the allocation-free

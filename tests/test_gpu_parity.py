@@ -362,17 +362,20 @@ def test_graph_replay_and_determinism(P):
     assert sb["status"] == 0
 
 
-def test_cg_resident_and_global_forms_identical(P, monkeypatch):
-    """The CG keeps r^, q and y in shared memory when a block's rows fit
-    (meshes up to about 1.2M cells on GB300) and in global memory otherwise;
-    both forms do the same arithmetic in the same order, so a mesh created
-    with FVGB_CG_RESIDENT=0 (global form only) gives the same bits."""
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cg_resident_and_global_forms_identical(P, monkeypatch, precision):
+    """The CG keeps its row-local vectors (FP64: r^, q, y; mixed precision:
+    the FP32 r^, q, e, w, v) in shared memory when a block's rows fit (meshes
+    up to about 1.2M cells on GB300) and in global memory otherwise; both
+    forms do the same arithmetic in the same order, so a mesh created with
+    FVGB_CG_RESIDENT=0 (global forms only) gives the same bits."""
     m = mg.permute_cells(mg.cavity3d(24), mg.random_permutation(24 ** 3, 5))
+    prec = P.FV_PREC_FP64 if precision == "fp64" else P.FV_PREC_MIXED
     out = []
     for env in ("1", "0"):
         monkeypatch.setenv("FVGB_CG_RESIDENT", env)
         mesh = P.Mesh(m, renumber=True)
-        case = P.Case(mesh, 0.01)
+        case = P.Case(mesh, 0.01, prec)
         its = []
         for _ in range(3):
             s = case.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
