@@ -191,7 +191,12 @@ fv_status fv_case_set_fields(fv_case *cs, const double *u, const double *p, cons
                              int32_t original_order);
 fv_status fv_case_get_fields(const fv_case *cs, double *u, double *p, double *phi,
                              int32_t original_order);
-/* Same with host buffers (copies through pinned staging; synchronous). */
+/* Same with host buffers; synchronous (the caller's buffers may be reused or
+ * read on return).  Where the device reaches pageable host memory through the
+ * host's page tables (NVLink-C2C systems such as GB300), the copy and
+ * permutation kernels read and write the caller's buffers directly; elsewhere,
+ * or with the environment variable FVGB_HOST_STAGING=1 at mesh creation, each
+ * field goes through a pinned staging buffer.  Same values either way. */
 fv_status fv_case_set_fields_host(fv_case *cs, const double *u, const double *p,
                                   const double *phi, int32_t original_order);
 fv_status fv_case_get_fields_host(const fv_case *cs, double *u, double *p, double *phi,

@@ -246,15 +246,15 @@ extern "C" fv_status fv_case_set_fields(fv_case *c, const double *u, const doubl
     fv_status st;
     if (u) {
         if (original_order) { if ((st = launch_permute_cells(m, 3, u, c->u, 1)) != FV_OK) return st; }
-        else FV_CUDA(cudaMemcpyAsync(c->u, u, sizeof(double) * 3 * m->N, cudaMemcpyDeviceToDevice, m->stream));
+        else FV_CUDA(cudaMemcpyAsync(c->u, u, sizeof(double) * 3 * m->N, cudaMemcpyDefault, m->stream));
     }
     if (p) {
         if (original_order) { if ((st = launch_permute_cells(m, 1, p, c->p, 1)) != FV_OK) return st; }
-        else FV_CUDA(cudaMemcpyAsync(c->p, p, sizeof(double) * m->N, cudaMemcpyDeviceToDevice, m->stream));
+        else FV_CUDA(cudaMemcpyAsync(c->p, p, sizeof(double) * m->N, cudaMemcpyDefault, m->stream));
     }
     if (phi) {
         if (original_order) { if ((st = launch_permute_faces(m, phi, c->phi, 1)) != FV_OK) return st; }
-        else FV_CUDA(cudaMemcpyAsync(c->phi, phi, sizeof(double) * m->M, cudaMemcpyDeviceToDevice, m->stream));
+        else FV_CUDA(cudaMemcpyAsync(c->phi, phi, sizeof(double) * m->M, cudaMemcpyDefault, m->stream));
     }
     return FV_OK;
 }
@@ -267,25 +267,35 @@ extern "C" fv_status fv_case_get_fields(const fv_case *c, double *u, double *p, 
     fv_status st;
     if (u) {
         if (original_order) { if ((st = launch_permute_cells(m, 3, c->u, u, 0)) != FV_OK) return st; }
-        else FV_CUDA(cudaMemcpyAsync(u, c->u, sizeof(double) * 3 * m->N, cudaMemcpyDeviceToDevice, m->stream));
+        else FV_CUDA(cudaMemcpyAsync(u, c->u, sizeof(double) * 3 * m->N, cudaMemcpyDefault, m->stream));
     }
     if (p) {
         if (original_order) { if ((st = launch_permute_cells(m, 1, c->p, p, 0)) != FV_OK) return st; }
-        else FV_CUDA(cudaMemcpyAsync(p, c->p, sizeof(double) * m->N, cudaMemcpyDeviceToDevice, m->stream));
+        else FV_CUDA(cudaMemcpyAsync(p, c->p, sizeof(double) * m->N, cudaMemcpyDefault, m->stream));
     }
     if (phi) {
         if (original_order) { if ((st = launch_permute_faces(m, c->phi, phi, 0)) != FV_OK) return st; }
-        else FV_CUDA(cudaMemcpyAsync(phi, c->phi, sizeof(double) * m->M, cudaMemcpyDeviceToDevice, m->stream));
+        else FV_CUDA(cudaMemcpyAsync(phi, c->phi, sizeof(double) * m->M, cudaMemcpyDefault, m->stream));
     }
     return FV_OK;
 }
 
-// Host variants: one pinned staging buffer, one device temporary.
+// Host variants.  Where the device reaches pageable host memory through the
+// host's page tables (GB300 with NVLink-C2C), the copy and permutation
+// kernels read or write the caller's buffers directly (m->host_direct);
+// otherwise each field goes through one pinned staging buffer and one device
+// temporary.  Both return once the caller's buffers may be reused or read.
 extern "C" fv_status fv_case_set_fields_host(fv_case *c, const double *u, const double *p,
                                              const double *phi, int32_t original_order)
 {
     FV_CHECK(c, FV_E_INVALID, "NULL case");
     const fv_mesh *m = c->mesh;
+    if (m->host_direct) {
+        const fv_status sd = fv_case_set_fields(c, u, p, phi, original_order);
+        if (sd != FV_OK) return sd;
+        FV_CUDA(cudaStreamSynchronize(m->stream));
+        return FV_OK;
+    }
     const size_t n3 = 3 * (size_t)m->N, n1 = m->N, nm = m->M;
     fv_status st = stage(c, sizeof(double) * (n3 > nm ? n3 : nm));
     if (st != FV_OK) return st;
@@ -308,6 +318,12 @@ extern "C" fv_status fv_case_get_fields_host(const fv_case *cc, double *u, doubl
     FV_CHECK(cc, FV_E_INVALID, "NULL case");
     fv_case *c = const_cast<fv_case *>(cc);
     const fv_mesh *m = c->mesh;
+    if (m->host_direct) {
+        const fv_status sd = fv_case_get_fields(c, u, p, phi, original_order);
+        if (sd != FV_OK) return sd;
+        FV_CUDA(cudaStreamSynchronize(m->stream));
+        return FV_OK;
+    }
     const size_t n3 = 3 * (size_t)m->N, n1 = m->N, nm = m->M;
     fv_status st = stage(c, sizeof(double) * (n3 > nm ? n3 : nm));
     if (st != FV_OK) return st;

@@ -127,6 +127,7 @@ struct fv_mesh {
     int nonorth = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 0;
+    int host_direct = 0;              // kernels may read/write pageable host memory (see case.cu)
     std::vector<fv_patch> patches;
     fvgb::MeshPlan plan;              // host copy of the addressing
     fvgb::DeviceArena arena;

@@ -240,7 +240,16 @@ extern "C" fv_status fv_mesh_create(const fv_mesh_desc *desc, void *stream, fv_m
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        int pageable = 0, host_tables = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
         if (e != cudaSuccess) { delete m; return cuda_status(e, "device query"); }
+        // host-buffer field exchange straight from and to the caller's memory
+        // where the device reaches pageable memory through the host's page
+        // tables; FVGB_HOST_STAGING=1 keeps the pinned staging copy
+        const char *staging = std::getenv("FVGB_HOST_STAGING");
+        m->host_direct = pageable && host_tables && !(staging && std::atoi(staging) != 0);
         st = upload_mesh(m, desc);
         if (st == FV_OK) st = krylov_setup(m);
     } catch (const std::bad_alloc &) {

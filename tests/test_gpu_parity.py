@@ -407,6 +407,32 @@ def test_fields_roundtrip(P):
     assert np.array_equal(iu.cpu().numpy(), ou) and np.array_equal(iphi.cpu().numpy(), ophi)
 
 
+@pytest.mark.parametrize("staging", ["0", "1"])
+def test_host_field_exchange(P, monkeypatch, staging):
+    """Host-buffer set/get, with the kernels reading and writing the caller's
+    pageable memory directly (where the device supports it) and through the
+    pinned staging buffer (FVGB_HOST_STAGING=1): the values round-trip bit for
+    bit in both orders and agree with the device-buffer exchange."""
+    monkeypatch.setenv("FVGB_HOST_STAGING", staging)
+    m = mg.permute_cells(mg.cavity3d(7), mg.random_permutation(343, 4))
+    mesh = P.Mesh(m, renumber=True)
+    case = P.Case(mesh, 0.01)
+    rng = np.random.default_rng(8)
+    u, p, phi = rng.standard_normal((3, 343)), rng.standard_normal(343), rng.standard_normal(m.n_faces)
+    case.set_fields_host(u, p, phi)
+    hu, hp, hphi = case.get_fields_host()
+    assert np.array_equal(hu, u) and np.array_equal(hp, p) and np.array_equal(hphi, phi)
+    gu, gp, gphi = case.get_fields()
+    assert np.array_equal(gu.cpu().numpy(), u) and np.array_equal(gphi.cpu().numpy(), phi)
+    iu, ip, iphi = case.get_fields_host(original_order=False)
+    du, dp, dphi = case.get_fields(original_order=False)
+    assert np.array_equal(iu, du.cpu().numpy()) and np.array_equal(ip, dp.cpu().numpy())
+    assert np.array_equal(iphi, dphi.cpu().numpy())
+    case.set_fields_host(2.0 * iu, -ip, 0.5 * iphi, original_order=False)
+    hu2, hp2, hphi2 = case.get_fields_host()
+    assert np.array_equal(hu2, 2.0 * u) and np.array_equal(hp2, -p) and np.array_equal(hphi2, 0.5 * phi)
+
+
 # ------------------------------------------------------------ SIMPLE step --
 
 def test_simple_channel_outlet(P):
