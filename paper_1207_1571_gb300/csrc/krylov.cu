@@ -12,7 +12,10 @@
 // scalars.  Rows are owned by a fixed thread for the whole solve, so a
 // thread only reads other threads' data where the algorithm needs neighbour
 // values (matrix-vector products); the barrier's acquire orders those loads
-// after the writes of the previous phase.
+// after the writes of the previous phase.  The same ownership lets the CG
+// kernels keep their row-local vectors in shared memory for the whole solve
+// where a block's rows fit (the resident forms, k_pcg<true> and
+// k_pcg_mixed<true>).
 //
 // CG works on the symmetrically scaled system  D^-1/2 A D^-1/2 y = D^-1/2 b
 // with x = D^-1/2 y: in exact arithmetic this generates the same iterates,
