@@ -451,6 +451,9 @@ struct MixArgs {
 
 struct MixScalars {
     double nb, nr0, nr, thresh, rho, rho_ref, ratio, alpha, beta, mu, delta, shift;
+    double inv_mu;   // 1 / mu (the deflation coefficient of every inner iteration)
+    double rel2;     // kReliable^2 rho_ref: refresh once r^.r^ falls below it
+    double pred2;    // (thresh / ratio)^2: r^.r^ below it predicts convergence
     int phase;       // 0 run, 1 converged, 2 iteration budget used, 3 breakdown, 4 zero rhs
     int refresh;     // 1: refresh after this iteration, 2: refresh and restart p
     int restart;     // restart the search direction at the next iteration
@@ -543,6 +546,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
         sc.refresh = 0;
         sc.nr = 0.0;
         sc.mu = tot[0];
+        sc.inv_mu = 1.0 / tot[0];
         sc.deflate = (tot[0] > 0.0 && isfinite(tot[0])) ? 1 : 0;
     }
     __syncthreads();
@@ -605,6 +609,10 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             sc.rho = tot[1];
             sc.rho_ref = tot[1];
             sc.ratio = tot[1] > 0.0 ? sc.nr / sqrt(tot[1]) : 0.0;
+            // the inner iterations compare r^.r^ with squared thresholds (a
+            // square root and a divide on thread 0 per iteration saved)
+            sc.rel2 = kReliable * kReliable * sc.rho_ref;
+            sc.pred2 = sc.ratio > 0.0 ? (sc.thresh / sc.ratio) * (sc.thresh / sc.ratio) : INFINITY;
             sc.delta = sc.deflate ? tot[2] / sc.mu : 0.0;
             sc.alpha = 0.0;          // the correction was folded into x
             sc.refresh = 0;
@@ -671,15 +679,14 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             if (threadIdx.x == 0) {
                 const double rn = tot[0];
                 if (!isfinite(rn)) { sc.refresh = 2; }
-                else if (rn <= kReliable * kReliable * sc.rho_ref ||
-                         sc.ratio * sqrt(rn) <= sc.thresh || it >= a.maxit) {
+                else if (rn <= sc.rel2 || rn <= sc.pred2 || it >= a.maxit) {
                     // refresh; sc.rho keeps r.r of the previous iteration so
                     // that beta can be formed with the refreshed residual
                     sc.refresh = 1;
                 } else {
                     sc.beta = rn / sc.rho;
                     sc.rho = rn;
-                    sc.delta = sc.deflate ? tot[1] / sc.mu : 0.0;
+                    sc.delta = sc.deflate ? tot[1] * sc.inv_mu : 0.0;
                 }
             }
             __syncthreads();
