@@ -932,22 +932,28 @@ static fv_status launch_k_pcg(const fv_mesh *m, int G, CgArgs &a)
 
 // Dynamic shared memory a resident form may use: what a block can hold beyond
 // the kernel's static shared memory, provided one block per SM stays resident
-// with it (0: use the global form).
-static fv_status resident_room(const void *fn, bool allow, int *out)
+// with it.  0 (the global form) when the device cannot provide it; the
+// resident form is an optimisation, so a failing query clears its error and
+// leaves the global form in place instead of failing the mesh.
+static int resident_room(const void *fn, bool allow)
 {
-    *out = 0;
-    if (!allow) return FV_OK;
+    if (!allow) return 0;
     int dev = 0, optin = 0, per = 0;
     cudaFuncAttributes fa;
-    FV_CUDA(cudaGetDevice(&dev));
-    FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    FV_CUDA(cudaFuncGetAttributes(&fa, fn));
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
     const int room = optin - (int)fa.sharedSizeBytes;
-    if (room <= 0) return FV_OK;
-    FV_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, room));
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCgBlock, room));
-    if (per >= 1) *out = room;
-    return FV_OK;
+    if (room <= 0) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCgBlock, room) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return per >= 1 ? room : 0;
 }
 
 fv_status krylov_setup(fv_mesh *m)
@@ -962,9 +968,8 @@ fv_status krylov_setup(fv_mesh *m)
     {
         const char *env = std::getenv("FVGB_CG_RESIDENT");
         const bool allow = !(env && std::atoi(env) == 0);
-        fv_status st;
-        if ((st = resident_room((const void *)k_pcg<true>, allow, &w.cg_res_max)) != FV_OK) return st;
-        if ((st = resident_room((const void *)k_pcg_mixed<true>, allow, &w.mix_res_max)) != FV_OK) return st;
+        w.cg_res_max = resident_room((const void *)k_pcg<true>, allow);
+        w.mix_res_max = resident_room((const void *)k_pcg_mixed<true>, allow);
     }
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed<false>, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel cannot be resident");
