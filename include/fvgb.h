@@ -252,7 +252,11 @@ fv_status fv_piso_run_graph(fv_case *cs, const fv_piso_params *prm, int32_t n_st
  * stage is one launch over all cases: assembly and corrections over all
  * cells, the Krylov solves one block per case from a queue of cases ordered
  * by size.  precision: FV_PREC_FP64 or FV_PREC_MIXED (pressure solve as in
- * fv_pcg_solve_mixed, per case).  stream as in fv_mesh_create. */
+ * fv_pcg_solve_mixed, per case).  stream as in fv_mesh_create.  Errors:
+ * FV_E_INVALID for NULL arrays, n < 1, an unknown precision, a negative
+ * viscosity, a mesh description that fails fv_mesh_create's validation or a
+ * batch whose joined mesh exceeds int32 indexing; FV_E_NOMEM / FV_E_CUDA when
+ * memory runs out.  fv_batch_destroy releases everything (NULL is a no-op). */
 typedef struct fv_batch fv_batch;
 fv_status fv_batch_create(const fv_mesh_desc *descs, int32_t n, const double *nu,
                           const int32_t *p_ref_cells, int32_t precision, void *stream,
