@@ -177,6 +177,114 @@ def hex_box(nx: int, ny: int, nz: int, L=(1.0, 1.0, 1.0), side_patch=None,
                 np.concatenate(Cf, axis=1), C, V, patches, corner_cell=0)
 
 
+def geometric_nodes(n: int, L: float = 1.0, ratio: float = 1.0) -> np.ndarray:
+    """``n + 1`` node coordinates on ``[0, L]`` whose spacings grow by
+    ``ratio`` from one cell to the next (``h_{i+1} = ratio * h_i``)."""
+    h = ratio ** np.arange(n, dtype=np.float64)
+    x = np.concatenate([[0.0], np.cumsum(h)])
+    x *= L / x[-1]
+    x[-1] = L
+    return x
+
+
+def graded_box(xs, ys, zs, side_patch=None, patch_specs=None) -> Mesh:
+    """Orthogonal hexahedral mesh on the tensor grid of node coordinates
+    ``xs``, ``ys``, ``zs`` (strictly increasing; cell sizes may differ from
+    cell to cell).  Cell ``(i, j, k)`` gets index ``i + nx*(j + ny*k)``; its
+    centroid is the midpoint of its node intervals, face centres are the
+    midpoints of the faces.  On such a mesh the face between two cells is
+    generally not half-way between their centroids, which is what makes the
+    interpolation weight of a face differ from 1/2.  Patch arguments as
+    :func:`hex_box`."""
+    xs, ys, zs = (np.asarray(a, dtype=np.float64) for a in (xs, ys, zs))
+    for a in (xs, ys, zs):
+        assert a.ndim == 1 and a.size >= 2 and (np.diff(a) > 0).all()
+    nx, ny, nz = xs.size - 1, ys.size - 1, zs.size - 1
+    hx, hy, hz = np.diff(xs), np.diff(ys), np.diff(zs)
+    cx, cy, cz = 0.5 * (xs[:-1] + xs[1:]), 0.5 * (ys[:-1] + ys[1:]), 0.5 * (zs[:-1] + zs[1:])
+    N = nx * ny * nz
+    cid = lambda i, j, k: (i + nx * (j + ny * k)).astype(np.int64)
+    ii, jj, kk = (a.ravel() for a in np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz),
+                                                  indexing="ij"))
+    idx = cid(ii, jj, kk)
+    C = np.zeros((3, N))
+    C[0, idx], C[1, idx], C[2, idx] = cx[ii], cy[jj], cz[kk]
+    V = np.zeros(N)
+    V[idx] = hx[ii] * hy[jj] * hz[kk]
+
+    own, nei, S, Cf = [], [], [], []
+    z0 = lambda n: np.zeros(n)
+    i, j, k = (a.ravel() for a in np.meshgrid(np.arange(nx - 1), np.arange(ny), np.arange(nz),
+                                               indexing="ij"))
+    own.append(cid(i, j, k)); nei.append(cid(i + 1, j, k))
+    S.append(np.stack([hy[j] * hz[k], z0(i.size), z0(i.size)]))
+    Cf.append(np.stack([xs[i + 1], cy[j], cz[k]]))
+    i, j, k = (a.ravel() for a in np.meshgrid(np.arange(nx), np.arange(ny - 1), np.arange(nz),
+                                               indexing="ij"))
+    own.append(cid(i, j, k)); nei.append(cid(i, j + 1, k))
+    S.append(np.stack([z0(i.size), hx[i] * hz[k], z0(i.size)]))
+    Cf.append(np.stack([cx[i], ys[j + 1], cz[k]]))
+    i, j, k = (a.ravel() for a in np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz - 1),
+                                               indexing="ij"))
+    own.append(cid(i, j, k)); nei.append(cid(i, j, k + 1))
+    S.append(np.stack([z0(i.size), z0(i.size), hx[i] * hy[j]]))
+    Cf.append(np.stack([cx[i], cy[j], zs[k + 1]]))
+    F = sum(a.size for a in own)
+
+    def side_faces(side):
+        if side in ("xmin", "xmax"):
+            j, k = (a.ravel() for a in np.meshgrid(np.arange(ny), np.arange(nz), indexing="ij"))
+            lo = side == "xmin"
+            i = np.full_like(j, 0 if lo else nx - 1)
+            area = np.stack([(-1.0 if lo else 1.0) * hy[j] * hz[k], z0(j.size), z0(j.size)])
+            cf = np.stack([np.full(j.size, xs[0] if lo else xs[-1]), cy[j], cz[k]])
+        elif side in ("ymin", "ymax"):
+            i, k = (a.ravel() for a in np.meshgrid(np.arange(nx), np.arange(nz), indexing="ij"))
+            lo = side == "ymin"
+            j = np.full_like(i, 0 if lo else ny - 1)
+            area = np.stack([z0(i.size), (-1.0 if lo else 1.0) * hx[i] * hz[k], z0(i.size)])
+            cf = np.stack([cx[i], np.full(i.size, ys[0] if lo else ys[-1]), cz[k]])
+        else:
+            i, j = (a.ravel() for a in np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij"))
+            lo = side == "zmin"
+            k = np.full_like(i, 0 if lo else nz - 1)
+            area = np.stack([z0(i.size), z0(i.size), (-1.0 if lo else 1.0) * hx[i] * hy[j]])
+            cf = np.stack([cx[i], cy[j], np.full(i.size, zs[0] if lo else zs[-1])])
+        return cid(i, j, k), area, cf
+
+    if side_patch is None:
+        side_patch = {s: "walls" for s in _SIDES}
+    if patch_specs is None:
+        patch_specs = {"walls": (WALL, (0.0, 0.0, 0.0), 0.0)}
+    patches, start = [], 0
+    for pname, (ptype, pu, pp) in patch_specs.items():
+        size = 0
+        for side in _SIDES:
+            if side_patch[side] != pname:
+                continue
+            o, a, cf = side_faces(side)
+            own.append(o); S.append(a); Cf.append(cf)
+            size += o.size
+        patches.append(Patch(pname, int(ptype), start, size, tuple(float(x) for x in pu), float(pp)))
+        start += size
+    owner = np.concatenate(own).astype(np.int32)
+    neighbour = np.concatenate(nei).astype(np.int32)
+    assert owner.size == F + start and neighbour.size == F
+    return Mesh(N, F, start, owner, neighbour, np.concatenate(S, axis=1),
+                np.concatenate(Cf, axis=1), C, V, patches, corner_cell=0)
+
+
+def graded_cavity3d(n: int, ratio: float = 1.3, u_lid: float = 1.0, L: float = 1.0) -> Mesh:
+    """The 3-D lid-driven cavity of :func:`cavity3d` on a graded mesh: the
+    cell sizes grow by ``ratio`` from cell to cell along every axis."""
+    x = geometric_nodes(n, L, ratio)
+    sp = {s: "fixedWalls" for s in _SIDES}
+    sp["ymax"] = "movingWall"
+    specs = {"movingWall": (WALL, (u_lid, 0.0, 0.0), 0.0),
+             "fixedWalls": (WALL, (0.0, 0.0, 0.0), 0.0)}
+    return graded_box(x, x, x, sp, specs)
+
+
 def cavity3d(n: int, u_lid: float = 1.0, L: float = 1.0) -> Mesh:
     """3-D lid-driven cavity on the cube ``[0,L]^3`` with ``n^3`` hexahedra.
 

@@ -24,6 +24,23 @@
  * Arithmetic rules: straight sequential loops, sums in face order or cell
  * order, no blocking, no reordering.  Built with -O2 -ffp-contract=off.
  *
+ * Parallel build (-fopenmp -DORC_PARALLEL, liborc_omp.so), used for the
+ * full-size workloads and the timed CPU baseline: the same source with two
+ * differences, both confined to the helpers marked ORC_PARALLEL below.
+ *  (1) Dot products and norms sum fixed blocks of 4096 consecutive terms in
+ *      element order and then add the block sums pairwise in block order, so
+ *      the result does not depend on the number of threads; only the
+ *      rounding of the sums differs from the sequential build.
+ *  (2) Inside the Krylov solvers the LDU product runs row by row over
+ *      threads, each row adding its terms in exactly the order of the
+ *      sequential face loop (diagonal, then the faces where the row is the
+ *      neighbour in face order, then the faces it owns in face order -- the
+ *      order the face loop produces when internal faces are sorted by
+ *      (owner, neighbour), as every oracle mesh's are); products are
+ *      therefore bit-identical.  Element-wise vector updates run over
+ *      threads with unchanged arithmetic.
+ * Everything else (assembly, corrections, renumbering) stays sequential.
+ *
  * Storage: vectors of 3 components are stored component-major (SoA):
  * x[c*n + i].  All arrays inside an omesh / ocase are in the renumbered
  * ("internal") cell and face order.
@@ -77,11 +94,62 @@ int orc_amg_pcg(struct oamg_s *h, const double *diag, const double *upper, const
 /* small vector helpers (sequential)                                         */
 /* ------------------------------------------------------------------------ */
 
+#ifdef ORC_PARALLEL
+#include <omp.h>
+#define ORC_FOR _Pragma("omp parallel for schedule(static)")
+enum { ORC_DOT_BLOCK = 4096 };
+
+/* fixed-block dot product: block sums in element order, then pairwise
+ * combination in block order (independent of the thread count) */
+static double dot_n(int n, const double *a, const double *b)
+{
+    int nb = (n + ORC_DOT_BLOCK - 1) / ORC_DOT_BLOCK;
+    if (nb <= 1) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += a[i] * b[i];
+        return s;
+    }
+    double *part = malloc(sizeof(double) * (size_t)nb);
+    if (!part) abort();
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nb; ++k) {
+        int lo = k * ORC_DOT_BLOCK, hi = lo + ORC_DOT_BLOCK < n ? lo + ORC_DOT_BLOCK : n;
+        double s = 0.0;
+        for (int i = lo; i < hi; ++i) s += a[i] * b[i];
+        part[k] = s;
+    }
+    while (nb > 1) {
+        int h = nb / 2;
+        for (int k = 0; k < h; ++k) part[k] = part[2 * k] + part[2 * k + 1];
+        if (nb & 1) part[h] = part[nb - 1];
+        nb = h + (nb & 1);
+    }
+    double s = part[0];
+    free(part);
+    return s;
+}
+
+void orc_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }
+int orc_threads(void) { return omp_get_max_threads(); }
+#else
+#define ORC_FOR
 static double dot_n(int n, const double *a, const double *b)
 {
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += a[i] * b[i];
     return s;
+}
+
+void orc_set_threads(int n) { (void)n; }
+int orc_threads(void) { return 1; }
+#endif
+int orc_parallel_build(void)
+{
+#ifdef ORC_PARALLEL
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 static double norm2_n(int n, const double *a) { return sqrt(dot_n(n, a, a)); }
@@ -353,6 +421,67 @@ void orc_ldu_matvec(int N, int F, const int *own, const int *nei, const double *
     ldu_matvec(N, F, own, nei, diag, upper, lower, x, y);
 }
 
+/* The Krylov solvers' product.  Sequential build: the face loop above.
+ * Parallel build (when the internal faces are sorted by (owner, neighbour)):
+ * row i adds diag_i x_i, then lower_f x_own[f] over the faces whose
+ * neighbour is i in face order, then upper_f x_nei[f] over the faces it owns
+ * in face order -- the face loop's own order of additions into y_i. */
+typedef struct {
+    int ok;                  /* 1 when the row form is in use */
+    int *lo_ptr, *lo_face;   /* faces with neighbour i: lo_face[lo_ptr[i] ..] */
+    int *up_ptr;             /* faces owned by i: up_ptr[i] .. up_ptr[i+1]-1 */
+} orows;
+
+static void rows_init(orows *R, int N, int F, const int *own, const int *nei)
+{
+    memset(R, 0, sizeof(*R));
+#ifdef ORC_PARALLEL
+    for (int f = 1; f < F; ++f)
+        if (own[f] < own[f - 1] || (own[f] == own[f - 1] && nei[f] <= nei[f - 1])) return;
+    for (int f = 0; f < F; ++f)
+        if (!(own[f] < nei[f]) || own[f] < 0 || nei[f] >= N) return;
+    R->lo_ptr = xcalloc((size_t)N + 1, sizeof(int));
+    R->lo_face = xcalloc(F ? F : 1, sizeof(int));
+    R->up_ptr = xcalloc((size_t)N + 1, sizeof(int));
+    for (int f = 0; f < F; ++f) { R->lo_ptr[nei[f] + 1]++; R->up_ptr[own[f] + 1]++; }
+    for (int i = 0; i < N; ++i) {
+        R->lo_ptr[i + 1] += R->lo_ptr[i];
+        R->up_ptr[i + 1] += R->up_ptr[i];
+    }
+    int *fill = xcalloc((size_t)N, sizeof(int));
+    for (int f = 0; f < F; ++f) R->lo_face[R->lo_ptr[nei[f]] + fill[nei[f]]++] = f;
+    free(fill);
+    R->ok = 1;
+#else
+    (void)N; (void)F; (void)own; (void)nei;
+#endif
+}
+
+static void rows_free(orows *R)
+{
+    free(R->lo_ptr); free(R->lo_face); free(R->up_ptr);
+}
+
+static void krylov_matvec(const orows *R, int N, int F, const int *own, const int *nei,
+                          const double *diag, const double *upper, const double *lower,
+                          const double *x, double *y)
+{
+    if (!R->ok) {
+        ldu_matvec(N, F, own, nei, diag, upper, lower, x, y);
+        return;
+    }
+    ORC_FOR
+    for (int i = 0; i < N; ++i) {
+        double s = diag[i] * x[i];
+        for (int k = R->lo_ptr[i]; k < R->lo_ptr[i + 1]; ++k) {
+            int f = R->lo_face[k];
+            s += lower[f] * x[own[f]];
+        }
+        for (int f = R->up_ptr[i]; f < R->up_ptr[i + 1]; ++f) s += upper[f] * x[nei[f]];
+        y[i] = s;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Jacobi-preconditioned CG (paper Sec. 3 and Sec. 4.3.2: SMVP, daxpy, dot,  */
 /* reduction and the diagonal preconditioner).                               */
@@ -377,37 +506,47 @@ int orc_pcg(int N, int F, const int *own, const int *nei, const double *diag,
         free(r); free(z); free(p); free(q);
         return 0;
     }
-    ldu_matvec(N, F, own, nei, diag, upper, upper, x, q);
+    orows R;
+    rows_init(&R, N, F, own, nei);
+    krylov_matvec(&R, N, F, own, nei, diag, upper, upper, x, q);
+    ORC_FOR
     for (int i = 0; i < N; ++i) r[i] = b[i] - q[i];
     double nr = norm2_n(N, r);
     double thresh = tol * nb;
     if (reltol * nr > thresh) thresh = reltol * nr;
     *res0_out = nr / nb;
     if (nr <= thresh) goto done;
+    ORC_FOR
     for (int i = 0; i < N; ++i) z[i] = r[i] / diag[i];
+    ORC_FOR
     for (int i = 0; i < N; ++i) p[i] = z[i];
     double rho = dot_n(N, r, z);
     for (it = 1; it <= maxit; ++it) {
-        ldu_matvec(N, F, own, nei, diag, upper, upper, p, q);
+        krylov_matvec(&R, N, F, own, nei, diag, upper, upper, p, q);
         double pq = dot_n(N, p, q);
         if (!(pq > 0.0) || !isfinite(pq)) { status = -2; break; }
         double alpha = rho / pq;
+        ORC_FOR
         for (int i = 0; i < N; ++i) x[i] += alpha * p[i];
+        ORC_FOR
         for (int i = 0; i < N; ++i) r[i] -= alpha * q[i];
         nr = norm2_n(N, r);
         if (!isfinite(nr)) { status = -2; break; }
         if (nr <= thresh) break;
         if (it == maxit) { status = -1; break; }
+        ORC_FOR
         for (int i = 0; i < N; ++i) z[i] = r[i] / diag[i];
         double rho_new = dot_n(N, r, z);
         double beta = rho_new / rho;
         rho = rho_new;
+        ORC_FOR
         for (int i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
     }
     if (it > maxit) status = -1;
 done:
     *res_out = nr / nb;
     *iters_out = it > maxit ? maxit : it;
+    rows_free(&R);
     free(r); free(z); free(p); free(q);
     return status;
 }
@@ -435,7 +574,10 @@ int orc_bicgstab(int N, int F, const int *own, const int *nei, const double *dia
         *res0_out = 0.0; *res_out = 0.0; *iters_out = 0;
         goto out;
     }
-    ldu_matvec(N, F, own, nei, diag, upper, lower, x, t);
+    orows R;
+    rows_init(&R, N, F, own, nei);
+    krylov_matvec(&R, N, F, own, nei, diag, upper, lower, x, t);
+    ORC_FOR
     for (int i = 0; i < N; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; }
     nr = norm2_n(N, r);
     double thresh = tol * nb;
@@ -446,22 +588,29 @@ int orc_bicgstab(int N, int F, const int *own, const int *nei, const double *dia
     for (it = 1; it <= maxit; ++it) {
         double rho = dot_n(N, rh, r);
         if (it == 1) {
+            ORC_FOR
             for (int i = 0; i < N; ++i) p[i] = r[i];
         } else {
             double beta = (rho / rho_old) * (alpha / omega);
+            ORC_FOR
             for (int i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
         }
+        ORC_FOR
         for (int i = 0; i < N; ++i) y[i] = p[i] / diag[i];
-        ldu_matvec(N, F, own, nei, diag, upper, lower, y, v);
+        krylov_matvec(&R, N, F, own, nei, diag, upper, lower, y, v);
         double rv = dot_n(N, rh, v);
         if (rv == 0.0 || !isfinite(rv)) { status = -2; break; }
         alpha = rho / rv;
+        ORC_FOR
         for (int i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
+        ORC_FOR
         for (int i = 0; i < N; ++i) z[i] = s[i] / diag[i];
-        ldu_matvec(N, F, own, nei, diag, upper, lower, z, t);
+        krylov_matvec(&R, N, F, own, nei, diag, upper, lower, z, t);
         double ts = dot_n(N, t, s), tt = dot_n(N, t, t);
         omega = tt > 0.0 ? ts / tt : 0.0;
+        ORC_FOR
         for (int i = 0; i < N; ++i) x[i] += alpha * y[i] + omega * z[i];
+        ORC_FOR
         for (int i = 0; i < N; ++i) r[i] = s[i] - omega * t[i];
         nr = norm2_n(N, r);
         if (!isfinite(nr)) { status = -2; break; }
@@ -474,6 +623,7 @@ int orc_bicgstab(int N, int F, const int *own, const int *nei, const double *dia
 done:
     *res_out = nr / nb;
     *iters_out = it > maxit ? maxit : it;
+    rows_free(&R);
 out:
     free(r); free(rh); free(p); free(v); free(y); free(s); free(z); free(t);
     return status;

@@ -126,6 +126,7 @@ struct fv_mesh {
     int N = 0, F = 0, B = 0, M = 0, np = 0;
     int nonorth = 0;
     cudaStream_t stream = nullptr;
+    int device = 0;                   // CUDA device current at fv_mesh_create
     int sm_count = 0;
     int host_direct = 0;              // kernels may read/write pageable host memory (see case.cu)
     std::vector<fv_patch> patches;

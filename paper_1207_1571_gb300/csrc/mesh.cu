@@ -239,6 +239,7 @@ extern "C" fv_status fv_mesh_create(const fv_mesh_desc *desc, void *stream, fv_m
         m->stream = static_cast<cudaStream_t>(stream);
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
+        m->device = dev;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev);
         int pageable = 0, host_tables = 0;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);

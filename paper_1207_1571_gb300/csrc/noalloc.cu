@@ -12,6 +12,7 @@
 // library stays loaded, and every call uses the same array.
 #include <mutex>
 
+#include "coop.cuh"
 #include "fvgb_internal.h"
 
 namespace fvgb {
@@ -26,7 +27,9 @@ constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 constexpr size_t kOffBar = 0;
 constexpr size_t kOffStats = align256(kOffBar + sizeof(GridBar));
 constexpr size_t kOffParts = align256(kOffStats + sizeof(DevSolveStats));
-constexpr size_t kOffVec = align256(kOffParts + sizeof(double) * 2 * kNoAllocMaxBlocks * 8);
+// two partial-sum records of kParts doubles per block (launch_pcg_scratch
+// places the second at max_blocks * kParts)
+constexpr size_t kOffVec = align256(kOffParts + sizeof(double) * 2 * kNoAllocMaxBlocks * kParts);
 constexpr size_t kVecBytes = align256(sizeof(double) * (size_t)kNoAllocMaxCells);
 constexpr size_t kOffVal = kOffVec + 5 * kVecBytes;
 constexpr size_t kScratchBytes = align256(kOffVal + sizeof(double) * (size_t)kNoAllocMaxEntries);
@@ -38,10 +41,14 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 unsigned char *g_addr[kMaxDevices] = {};
 
-fv_status scratch_address(unsigned char **out)
+// The array's address on the mesh's device.  cudaGetSymbolAddress answers
+// for the current device, so the current device must be the mesh's.
+fv_status scratch_address(const fv_mesh *m, unsigned char **out)
 {
     int dev = 0;
     FV_CUDA(cudaGetDevice(&dev));
+    FV_CHECK(dev == m->device, FV_E_INVALID,
+             "fv_pcg_solve_noalloc: current device %d is not the mesh's device %d", dev, m->device);
     FV_CHECK(dev >= 0 && dev < kMaxDevices, FV_E_UNSUPPORTED, "device %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
@@ -72,7 +79,7 @@ extern "C" fv_status fv_pcg_solve_noalloc(const fv_mesh *mc, const double *diag,
              "fv_pcg_solve_noalloc handles at most %d row entries (mesh has %d)",
              kNoAllocMaxEntries, mc->nnz);
     unsigned char *base = nullptr;
-    fv_status st = scratch_address(&base);
+    fv_status st = scratch_address(mc, &base);
     if (st != FV_OK) return st;
     CgScratch ws;
     ws.bar = reinterpret_cast<GridBar *>(base + kOffBar);

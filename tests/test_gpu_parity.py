@@ -236,6 +236,42 @@ def test_piso_3d_cavity_permuted(P):
     assert_fields(case, oc)
 
 
+def _cavity_patches():
+    sides = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
+    sp = {k: "fixedWalls" for k in sides}
+    sp["ymax"] = "movingWall"
+    return sp, {"movingWall": (mg.WALL, (1.0, 0.0, 0.0), 0.0),
+                "fixedWalls": (mg.WALL, (0.0, 0.0, 0.0), 0.0)}
+
+
+def test_piso_graded_cavity(P):
+    """The 3-D cavity on a graded mesh (cell sizes growing by 1.15 from cell
+    to cell along x and z and shrinking by the same factor along y, so the
+    face interpolation weights are 0.465 or 0.535 instead of 1/2), cells
+    permuted: 8 PISO steps in lockstep with the oracle, whose weight
+    convention the graded-mesh pins fix."""
+    n = 14
+    up, down = mg.geometric_nodes(n, 1.0, 1.15), mg.geometric_nodes(n, 1.0, 1.0 / 1.15)
+    m = mg.graded_box(up, down, up, *_cavity_patches())
+    m = mg.permute_cells(m, mg.random_permutation(n ** 3, 77))
+    mesh, case, om, oc = both(P, m, 0.01)
+    g = om.geometry()
+    assert np.abs(g["w"] - 0.5).min() > 0.03
+    for step in range(8):
+        s = case.piso_step(0.01, 2, p_ref_cell=m.corner_cell)
+        so = oc.piso_step(0.01, 2, p_ref_cell=m.corner_cell)
+        assert s["status"] == 0
+        assert_iters(s, so)
+    assert_fields(case, oc)
+    # the Gauss gradient of a linear field is exact on this mesh (to rounding)
+    cell, face, _ = om.orders()
+    C = np.empty_like(m.C); C[:, cell] = m.C
+    Cf = np.empty_like(m.Cf); Cf[:, face] = m.Cf
+    a = np.array([0.3, -1.7, 2.5])
+    gr = mesh.gauss_grad(t64(a @ C), t64(a @ Cf[:, m.n_internal_faces:])).cpu().numpy()
+    assert np.abs(gr - a[:, None]).max() < 1e-11
+
+
 def test_piso_tets_nonorthogonal(P):
     m = mg.tet_box(4, 4, 4, jitter=0.1)
     m.patches[0].u = (1.0, 0.0, 0.0)

@@ -113,3 +113,17 @@ def test_batch_sampler():
     assert ns.min() >= 32 and ns.max() <= 128
     assert re.min() >= 10.0 and re.max() <= 1000.0
     assert cases == mg.batch_cases()
+
+
+def test_graded_box_reduces_to_uniform_box():
+    # equal spacing gives the uniform generator's mesh (same numbering,
+    # same faces, geometry to rounding)
+    u = mg.hex_box(5, 4, 3, (1.0, 2.0, 0.6))
+    g = mg.graded_box(mg.geometric_nodes(5, 1.0, 1.0), mg.geometric_nodes(4, 2.0, 1.0),
+                      mg.geometric_nodes(3, 0.6, 1.0))
+    assert np.array_equal(u.owner, g.owner) and np.array_equal(u.neighbour, g.neighbour)
+    for a in ("Sf", "Cf", "C", "V"):
+        assert np.allclose(getattr(u, a), getattr(g, a), rtol=0, atol=1e-15), a
+    x = mg.geometric_nodes(6, 2.0, 1.3)
+    h = np.diff(x)
+    assert x[0] == 0.0 and x[-1] == 2.0 and np.allclose(h[1:] / h[:-1], 1.3, rtol=1e-13)
