@@ -501,6 +501,201 @@ def duct_inlet_profile(Cf_xy: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Mixed-element meshes: hexahedra, triangular prisms and pyramids
+# ---------------------------------------------------------------------------
+
+def polyhedral_mesh(X, cells, L, side_patch=None, patch_specs=None) -> Mesh:
+    """Face-addressed mesh of polyhedral cells.  ``X`` (3, n_nodes) node
+    coordinates; ``cells`` a list of cells, each a list of faces, each face a
+    list of node indices in cyclic order (either orientation).  Faces shared
+    by two cells become internal faces (owner = the cell listed first),
+    the others boundary faces, assigned to the box sides of ``[0,L]``
+    (``hex_box`` patch arguments).
+
+    Geometry of possibly non-planar faces and of the cells, by the usual
+    decomposition: a face is split into triangles around the mean of its
+    nodes; its area vector is the sum of theirs and its centre their
+    area-weighted centroid.  A cell is split into the tetrahedra spanned by
+    the mean of its nodes and those face triangles; its volume and centroid
+    are theirs summed and volume-averaged.  Area vectors point out of the
+    owner."""
+    X = np.asarray(X, dtype=np.float64)
+    Lx, Ly, Lz = (float(v) for v in L)
+
+    def face_geom(nodes):
+        P = X[:, nodes]
+        xc = P.mean(axis=1)
+        Pn = np.roll(P, -1, axis=1)
+        s = 0.5 * np.cross(Pn - P, xc[:, None] - P, axis=0)
+        c = (P + Pn + xc[:, None]) / 3.0
+        a = np.linalg.norm(s, axis=0)
+        return s.sum(axis=1), (c * a).sum(axis=1) / a.sum(), s, c
+
+    keys = {}
+    faces = []          # [nodes, owner, neighbour]
+    for ci, cf in enumerate(cells):
+        for nodes in cf:
+            k = tuple(sorted(nodes))
+            if k in keys:
+                f = faces[keys[k]]
+                assert f[2] < 0, "a face shared by more than two cells"
+                f[2] = ci
+            else:
+                keys[k] = len(faces)
+                faces.append([list(nodes), ci, -1])
+    geo = [face_geom(f[0]) for f in faces]
+    N = len(cells)
+    C = np.zeros((3, N))
+    V = np.zeros(N)
+    for ci, cf in enumerate(cells):
+        x0 = X[:, sorted({n for nodes in cf for n in nodes})].mean(axis=1)
+        vol, mom = 0.0, np.zeros(3)
+        for nodes in cf:
+            S, Cf, s, c = geo[keys[tuple(sorted(nodes))]]
+            sgn = 1.0 if S @ (Cf - x0) > 0 else -1.0
+            v = sgn * np.einsum("ij,ij->j", s, c - x0[:, None]) / 3.0
+            vol += v.sum()
+            mom += ((0.25 * x0[:, None] + 0.75 * c) * v).sum(axis=1)
+        V[ci] = vol
+        C[:, ci] = mom / vol
+    internal = [f for f in range(len(faces)) if faces[f][2] >= 0]
+    bnd = [f for f in range(len(faces)) if faces[f][2] < 0]
+
+    def oriented(f):
+        S, Cf = geo[f][0], geo[f][1]
+        o = faces[f][1]
+        return (S if S @ (Cf - C[:, o]) > 0 else -S), Cf
+
+    Si = np.array([oriented(f)[0] for f in internal]).T.reshape(3, -1)
+    Cfi = np.array([geo[f][1] for f in internal]).T.reshape(3, -1)
+    own_i = np.array([faces[f][1] for f in internal], np.int32)
+    nei_i = np.array([faces[f][2] for f in internal], np.int32)
+    Sb = np.array([oriented(f)[0] for f in bnd]).T.reshape(3, -1)
+    Cfb = np.array([geo[f][1] for f in bnd]).T.reshape(3, -1)
+    own_b = np.array([faces[f][1] for f in bnd], np.int32)
+    tol = 1e-9 * max(Lx, Ly, Lz)
+    side = np.full(len(bnd), -1)
+    for s_id, (ax, val) in enumerate([(0, 0.0), (0, Lx), (1, 0.0), (1, Ly), (2, 0.0), (2, Lz)]):
+        side[np.abs(Cfb[ax] - val) < tol] = s_id
+    assert (side >= 0).all()
+    if side_patch is None:
+        side_patch = {s: "walls" for s in _SIDES}
+    if patch_specs is None:
+        patch_specs = {"walls": (WALL, (0.0, 0.0, 0.0), 0.0)}
+    b_order, patches, start = [], [], 0
+    for pname, (ptype, pu, pp) in patch_specs.items():
+        sel = np.concatenate([np.nonzero(side == s_id)[0] for s_id, s in enumerate(_SIDES)
+                              if side_patch[s] == pname]).astype(np.int64)
+        b_order.append(sel)
+        patches.append(Patch(pname, int(ptype), start, sel.size, tuple(float(x) for x in pu), float(pp)))
+        start += sel.size
+    b_order = np.concatenate(b_order)
+    owner = np.concatenate([own_i, own_b[b_order]]).astype(np.int32)
+    Sf = np.concatenate([Si, Sb[:, b_order]], axis=1)
+    Cf = np.concatenate([Cfi, Cfb[:, b_order]], axis=1)
+    return Mesh(N, own_i.size, b_order.size, owner, nei_i, Sf, Cf, C, V, patches, corner_cell=0)
+
+
+def mixed_box(nx: int, ny: int, nz: int, L=(1.0, 1.0, 1.0), jitter: float = 0.0,
+              seed: int = 2024, prism_every: int = 3, pyramid_every: int = 4,
+              side_patch=None, patch_specs=None) -> Mesh:
+    """A conforming mixed-element mesh of the box ``[0,L]``: an ``nx*ny*nz``
+    hexahedral grid in which
+
+    * every hexahedron of the columns with ``(i + j) % prism_every == 0`` is
+      split into two triangular prisms by the vertical plane through its
+      (i, j) -> (i+1, j+1) diagonal (the whole column the same way, so the
+      prism caps match);
+    * outside those columns, every hexahedron with
+      ``(i + j + k) % pyramid_every == 1`` is split into six pyramids, one
+      on each of its faces, with their apex at a node added at its centre;
+    * the other cells stay hexahedra.
+
+    Interior nodes (grid nodes off the boundary and the added centre nodes)
+    are moved by ``U(-jitter*h, +jitter*h)`` per coordinate
+    (``numpy.random.default_rng(seed)``), so faces become non-planar and
+    the mesh non-orthogonal; boundary nodes stay, so the boundary stays
+    planar.  Cell (i, j, k)'s pieces are numbered in grid order."""
+    Lx, Ly, Lz = (float(v) for v in L)
+    h = np.array([Lx / nx, Ly / ny, Lz / nz])
+    NX, NY, NZ = nx + 1, ny + 1, nz + 1
+    nid = lambda i, j, k: i + NX * (j + NY * k)
+    I, J, K = (a.ravel() for a in np.meshgrid(np.arange(NX), np.arange(NY), np.arange(NZ),
+                                               indexing="ij"))
+    ng = NX * NY * NZ
+    Xg = np.zeros((3, ng))
+    Xg[0, nid(I, J, K)] = I * h[0]
+    Xg[1, nid(I, J, K)] = J * h[1]
+    Xg[2, nid(I, J, K)] = K * h[2]
+    interior = np.zeros(ng, bool)
+    interior[nid(I, J, K)] = (I > 0) & (I < nx) & (J > 0) & (J < ny) & (K > 0) & (K < nz)
+    pyr = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                if (i + j) % prism_every != 0 and (i + j + k) % pyramid_every == 1:
+                    pyr.append((i, j, k))
+    centre = {c: ng + q for q, c in enumerate(pyr)}
+    X = np.zeros((3, ng + len(pyr)))
+    X[:, :ng] = Xg
+    for (i, j, k), q in centre.items():
+        X[:, q] = (np.array([i, j, k]) + 0.5) * h
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        d = rng.uniform(-jitter, jitter, size=X.shape) * h[:, None]
+        movable = np.concatenate([interior, np.ones(len(pyr), bool)])
+        X[:, movable] += d[:, movable]
+
+    cells = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                n = {(a, b, c): nid(i + a, j + b, k + c) for a in (0, 1) for b in (0, 1)
+                     for c in (0, 1)}
+                quads = [[n[0, 0, 0], n[0, 1, 0], n[0, 1, 1], n[0, 0, 1]],
+                         [n[1, 0, 0], n[1, 0, 1], n[1, 1, 1], n[1, 1, 0]],
+                         [n[0, 0, 0], n[0, 0, 1], n[1, 0, 1], n[1, 0, 0]],
+                         [n[0, 1, 0], n[1, 1, 0], n[1, 1, 1], n[0, 1, 1]],
+                         [n[0, 0, 0], n[1, 0, 0], n[1, 1, 0], n[0, 1, 0]],
+                         [n[0, 0, 1], n[0, 1, 1], n[1, 1, 1], n[1, 0, 1]]]
+                if (i + j) % prism_every == 0:
+                    diag = [n[0, 0, 0], n[1, 1, 0], n[1, 1, 1], n[0, 0, 1]]
+                    cells.append([[n[0, 0, 0], n[1, 0, 0], n[1, 1, 0]],
+                                  [n[0, 0, 1], n[1, 0, 1], n[1, 1, 1]], quads[2], quads[1], diag])
+                    cells.append([[n[0, 0, 0], n[1, 1, 0], n[0, 1, 0]],
+                                  [n[0, 0, 1], n[1, 1, 1], n[0, 1, 1]], quads[0], quads[3], diag])
+                elif (i, j, k) in centre:
+                    c = centre[(i, j, k)]
+                    for q in quads:
+                        cells.append([q] + [[q[t], q[(t + 1) % 4], c] for t in range(4)])
+                else:
+                    cells.append(quads)
+    return polyhedral_mesh(X, cells, (Lx, Ly, Lz), side_patch, patch_specs)
+
+
+def mixed_cavity3d(n: int, jitter: float = 0.0, seed: int = 2024) -> Mesh:
+    """The 3-D lid-driven cavity of :func:`cavity3d` on a :func:`mixed_box`
+    mesh of the unit cube."""
+    sp = {s: "fixedWalls" for s in _SIDES}
+    sp["ymax"] = "movingWall"
+    specs = {"movingWall": (WALL, (1.0, 0.0, 0.0), 0.0),
+             "fixedWalls": (WALL, (0.0, 0.0, 0.0), 0.0)}
+    return mixed_box(n, n, n, (1.0, 1.0, 1.0), jitter, seed, side_patch=sp, patch_specs=specs)
+
+
+def mixed_duct(n: int, length_cells: int, jitter: float = 0.0, seed: int = 2024) -> Mesh:
+    """The square duct of :func:`duct_hex` on a :func:`mixed_box` mesh: inlet
+    ``z = 0``, outlet ``z = Lz`` (p = 0), four no-slip walls."""
+    Lz = length_cells / n
+    sp = {"xmin": "walls", "xmax": "walls", "ymin": "walls", "ymax": "walls",
+          "zmin": "inlet", "zmax": "outlet"}
+    specs = {"inlet": (INLET, (0.0, 0.0, 1.0), 0.0), "outlet": (OUTLET, (0.0, 0.0, 0.0), 0.0),
+             "walls": (WALL, (0.0, 0.0, 0.0), 0.0)}
+    return mixed_box(n, n, length_cells, (1.0, 1.0, Lz), jitter, seed, side_patch=sp,
+                     patch_specs=specs)
+
+
+# ---------------------------------------------------------------------------
 # Batch sampler (256 uneven 2-D cavities)
 # ---------------------------------------------------------------------------
 
