@@ -58,3 +58,51 @@ def assert_iters_where_well_conditioned(gpu_its, its0, its_p):
     bad = stable & (np.abs(gi - its0) > 1)
     assert not bad.any(), (np.argwhere(bad)[:5], gi[bad][:5], its0[bad][:5])
     return stable
+
+
+def field_errors(got, ref):
+    """Relative L2 errors of (u, p, phi) against the reference, with p split
+    into its mean-free part and its mean.  The pressure of a closed domain
+    is fixed only through the reference-cell pin, whose constant mode is the
+    near-null eigenvector of the pressure matrix; a tolerance-truncated CG
+    resolves that mode last, so the mean of p carries most of the rounding
+    sensitivity.  p_mean is |mean(p) - mean(p_ref)| relative to the RMS of
+    p_ref."""
+    (u, p, phi), (uo, po, phio) = got, ref
+    rms = np.sqrt(np.mean(np.asarray(po, float) ** 2))
+    return {"u": rel(u, uo), "phi": rel(phi, phio), "p": rel(p, po),
+            "p_meanfree": rel(p - np.mean(p), po - np.mean(po)),
+            "p_mean": abs(float(np.mean(p) - np.mean(po))) / (rms if rms > 0 else 1.0)}
+
+
+def oracle_spread(m, nu, nsteps, step, eps=1e-15, seeds=(1, 2), parallel=False):
+    """As :func:`oracle_envelope`, on one oracle mesh (optionally the OpenMP
+    build), with the spread of each entry of :func:`field_errors`: returns
+    (base case, per-step counts, perturbed per-step counts, spread dict)."""
+    om = O.Mesh(m, renumber=True, parallel=parallel)
+
+    def run(e, seed):
+        oc = O.Case(om, nu)
+        if e > 0:
+            u = np.zeros((3, m.n_cells))
+            u[:2] = e * np.random.default_rng(seed).standard_normal((2, m.n_cells))
+            oc.set_fields(u, np.zeros(m.n_cells), np.zeros(m.n_faces))
+        its = [np.array(step(oc, n)["iters"]) for n in range(nsteps)]
+        return oc, np.array(its)
+    base, its0 = run(0.0, 0)
+    f0 = base.get_fields()
+    spread = {}
+    its_p = []
+    for sd in seeds:
+        oc, its = run(eps, sd)
+        its_p.append(its)
+        for k, v in field_errors(oc.get_fields(), f0).items():
+            spread[k] = max(spread.get(k, 0.0), v)
+    return base, its0, its_p, spread
+
+
+def assert_errors_within(errs, spread=None, floor=TOL, factor=10.0, keys=None):
+    """Each error within max(floor, factor x the oracle's own spread)."""
+    for k in keys or ("u", "phi", "p_meanfree", "p_mean"):
+        bar = max(floor, factor * spread[k]) if spread else floor
+        assert errs[k] <= bar, (k, errs[k], bar)
