@@ -44,6 +44,7 @@ constexpr int kAmgNmin = 32;           // coarsest level size target
 constexpr int kAmgCoarseMax = 64;      // largest coarsest level handled on the device
 constexpr int kAmgBlock = 512;
 constexpr int kAmgBlockRows = 256;     // levels up to this size run inside block 0
+constexpr int kAmgShadowMax = 64 << 10; // largest shared-memory copy of those levels
 constexpr double kAmgTie = 1e-9;
 constexpr double kAmgOmega = 2.0 / 3.0;
 constexpr double kAmgAlpha = 1.8;
@@ -164,6 +165,7 @@ struct AmgData {
     int L = 0;                // index of the coarsest level
     int G = 1;                // levels 0..G-1 run over the whole grid
     int grid = 0;             // cooperative grid size
+    int shadow_bytes = 0;     // dynamic shared memory of block 0's copy of levels G..L (0: none)
     int n[kAmgMaxLev] = {}, ne[kAmgMaxLev] = {};
     AmgLevelDev *lev = nullptr;      // device copy of the level table
     int *coarse_ok = nullptr;
@@ -186,6 +188,7 @@ struct AmgArgs {
     const double *d0, *o0;     // level-0 matrix: diagonal [N] and edge coefficients [F]
     double o0_sign;            // o = o0_sign * o0[f] (-1 when o0 holds the positive a_f)
     int fp32;                  // the V-cycle in FP32 (mixed precision)
+    int shadow;                // block 0 keeps levels G..L in shared memory
     const double *b;
     double *x, *r, *z, *p, *q;
     double *partA, *partB;
@@ -350,10 +353,10 @@ __device__ void phase_galerkin_edges(const AmgArgs &a, int l, Span s, int t0, in
 
 // x = x + omega (b - A x) / d, from xin to xout
 template <class V>
-__device__ void phase_sweep(const AmgArgs &a, int l, const V *xin, V *xout, Span s, int t0,
+__device__ void phase_sweep(const AmgLevelDev *lv, int l, const V *xin, V *xout, Span s, int t0,
                             int step)
 {
-    const AmgLevelDev &L = a.lev[l];
+    const AmgLevelDev &L = lv[l];
     const V *b = VL<V>::b(L), *dinv = VL<V>::dinv(L);
     const V w = (V)kAmgOmega;
     for (int i = s.lo + t0; i < s.hi; i += step)
@@ -363,9 +366,9 @@ __device__ void phase_sweep(const AmgArgs &a, int l, const V *xin, V *xout, Span
 // b_{l+1} = P^T (b - A xa) over each aggregate, and the next level's first
 // sweep from zero: x_{l+1} = omega b_{l+1} / d_{l+1}.
 template <class V>
-__device__ void phase_restrict(const AmgArgs &a, int l, Span s, int t0, int step)
+__device__ void phase_restrict(const AmgLevelDev *lv, int l, Span s, int t0, int step)
 {
-    const AmgLevelDev &F = a.lev[l], &C = a.lev[l + 1];
+    const AmgLevelDev &F = lv[l], &C = lv[l + 1];
     const V *fb = VL<V>::b(F), *fxa = VL<V>::xa(F), *cdinv = VL<V>::dinv(C);
     V *cb = VL<V>::b(C), *cx = VL<V>::x(C);
     for (int I = s.lo + t0; I < s.hi; I += step) {
@@ -382,10 +385,10 @@ __device__ void phase_restrict(const AmgArgs &a, int l, Span s, int t0, int step
 // x = xa + alpha P e_c, then one sweep; neighbours' prolonged values are
 // formed on the fly.
 template <class V>
-__device__ void phase_prolong_sweep(const AmgArgs &a, int l, Span s, int t0, int step)
+__device__ void phase_prolong_sweep(const AmgLevelDev *lv, int l, Span s, int t0, int step)
 {
-    const AmgLevelDev &L = a.lev[l];
-    const V *ec = VL<V>::xa(a.lev[l + 1]);
+    const AmgLevelDev &L = lv[l];
+    const V *ec = VL<V>::xa(lv[l + 1]);
     const V *xa = VL<V>::xa(L), *sv = VL<V>::sval(L), *d = VL<V>::d(L);
     const V *b = VL<V>::b(L), *dinv = VL<V>::dinv(L);
     V *x = VL<V>::x(L);
@@ -444,9 +447,9 @@ __device__ bool coarse_factor(const AmgArgs &a, double *c)
 // xa_L = A_L^-1 b_L with the FP64 factor c (shared memory; warp 0 of block
 // 0), working vector y in shared memory
 template <class V>
-__device__ void coarse_solve(const AmgArgs &a, const double *c, double *y)
+__device__ void coarse_solve(const AmgArgs &a, const AmgLevelDev *lv, const double *c, double *y)
 {
-    const AmgLevelDev &C = a.lev[a.L];
+    const AmgLevelDev &C = lv[a.L];
     const int n = a.nc, lane = threadIdx.x & 31;
     const V *cb = VL<V>::b(C);
     V *cxa = VL<V>::xa(C);
@@ -470,27 +473,120 @@ __device__ void coarse_solve(const AmgArgs &a, const double *c, double *y)
     __syncwarp();
 }
 
-// The levels from G down to the coarsest and back, inside block 0.
+// The levels from G down to the coarsest and back, inside block 0, on the
+// level table lv (the shared-memory copy of those levels when it exists).
 template <class V>
-__device__ void block_levels_down_up(const AmgArgs &a, const double *chol, double *cy)
+__device__ void block_levels_down_up(const AmgArgs &a, const AmgLevelDev *lv, const double *chol,
+                                     double *cy)
 {
     const int t0 = threadIdx.x, step = blockDim.x;
     for (int l = a.G; l < a.L; ++l) {
-        const Span s{0, a.lev[l].n};
-        phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]), s, t0, step);
+        const Span s{0, lv[l].n};
+        phase_sweep<V>(lv, l, VL<V>::x(lv[l]), VL<V>::xa(lv[l]), s, t0, step);
         __syncthreads();
-        phase_restrict<V>(a, l, Span{0, a.lev[l + 1].n}, t0, step);
+        phase_restrict<V>(lv, l, Span{0, lv[l + 1].n}, t0, step);
         __syncthreads();
     }
-    if (threadIdx.x < 32) coarse_solve<V>(a, chol, cy);
+    if (threadIdx.x < 32) coarse_solve<V>(a, lv, chol, cy);
     __syncthreads();
     for (int l = a.L - 1; l >= a.G; --l) {
-        const Span s{0, a.lev[l].n};
-        phase_prolong_sweep<V>(a, l, s, t0, step);
+        const Span s{0, lv[l].n};
+        phase_prolong_sweep<V>(lv, l, s, t0, step);
         __syncthreads();
-        phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]), s, t0, step);
+        phase_sweep<V>(lv, l, VL<V>::x(lv[l]), VL<V>::xa(lv[l]), s, t0, step);
         __syncthreads();
     }
+}
+
+// Shared-memory copy of the levels G..L for block 0 (their matrices are
+// fixed for the solve once the Galerkin products are formed): the row
+// structure, coefficients, diagonal and its reciprocal, the vectors of the
+// cycle in value type V, the aggregate maps and the member lists the
+// restriction sums over.  Thread 0 lays the arrays out in `dyn` and fills
+// the level table `sl`; the block copies the arrays.  Level G's right-hand
+// side and first iterate come from the grid phase of every cycle and its
+// result goes back to it (shadow_in / shadow_out).
+template <class V>
+__device__ void shadow_setup(const AmgArgs &a, AmgLevelDev *sl, unsigned char *dyn)
+{
+    if (threadIdx.x == 0) {
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            unsigned char *p = dyn + off;
+            off += (bytes + 15) & ~(size_t)15;
+            return p;
+        };
+        for (int l = a.G; l <= a.L; ++l) {
+            const AmgLevelDev &g = a.lev[l];
+            AmgLevelDev &d = sl[l];
+            d = g;
+            const int n = g.n, nsl = (n + 31) >> 5;
+            const int slots = g.sptr[nsl];
+            V *sv = (V *)take(sizeof(V) * slots);
+            V *dd = (V *)take(sizeof(V) * n);
+            V *di = (V *)take(sizeof(V) * n);
+            V *bb = (V *)take(sizeof(V) * n);
+            V *xx = (V *)take(sizeof(V) * n);
+            V *xa = (V *)take(sizeof(V) * n);
+            if (sizeof(V) == 8) {
+                d.sval = (double *)sv; d.d = (double *)dd; d.dinv = (double *)di;
+                d.b = (double *)bb; d.x = (double *)xx; d.xa = (double *)xa;
+            } else {
+                d.sval32 = (float *)sv; d.d32 = (float *)dd; d.dinv32 = (float *)di;
+                d.b32 = (float *)bb; d.x32 = (float *)xx; d.xa32 = (float *)xa;
+            }
+            d.sptr = (const int32_t *)take(sizeof(int32_t) * (nsl + 1));
+            d.scol = (const int32_t *)take(sizeof(int32_t) * slots);
+            d.agg = l < a.L ? (const int32_t *)take(sizeof(int32_t) * n) : nullptr;
+            if (l > a.G) {
+                d.mptr = (const int32_t *)take(sizeof(int32_t) * (n + 1));
+                d.memb = (const int32_t *)take(sizeof(int32_t) * g.mptr[n]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = a.G; l <= a.L; ++l) {
+        const AmgLevelDev &g = a.lev[l], &d = sl[l];
+        const int n = g.n, nsl = (n + 31) >> 5;
+        const int slots = g.sptr[nsl];
+        V *sv = (V *)VL<V>::sval(d);
+        V *dd = (V *)VL<V>::d(d);
+        V *di = (V *)VL<V>::dinv(d);
+        for (int k = threadIdx.x; k < slots; k += blockDim.x) {
+            sv[k] = VL<V>::sval(g)[k];
+            ((int32_t *)d.scol)[k] = g.scol[k];
+        }
+        for (int k = threadIdx.x; k <= nsl; k += blockDim.x) ((int32_t *)d.sptr)[k] = g.sptr[k];
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            dd[k] = VL<V>::d(g)[k];
+            di[k] = VL<V>::dinv(g)[k];
+            if (l < a.L) ((int32_t *)d.agg)[k] = g.agg[k];
+        }
+        if (l > a.G) {
+            for (int k = threadIdx.x; k <= n; k += blockDim.x) ((int32_t *)d.mptr)[k] = g.mptr[k];
+            for (int k = threadIdx.x; k < g.mptr[n]; k += blockDim.x)
+                ((int32_t *)d.memb)[k] = g.memb[k];
+        }
+    }
+    __syncthreads();
+}
+
+template <class V>
+__device__ void shadow_in(const AmgArgs &a, const AmgLevelDev *sl)
+{
+    const AmgLevelDev &g = a.lev[a.G], &d = sl[a.G];
+    for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
+        VL<V>::b(d)[k] = VL<V>::b(g)[k];
+        VL<V>::x(d)[k] = VL<V>::x(g)[k];
+    }
+    __syncthreads();
+}
+
+template <class V>
+__device__ void shadow_out(const AmgArgs &a, const AmgLevelDev *sl)
+{
+    const AmgLevelDev &g = a.lev[a.G], &d = sl[a.G];
+    for (int k = threadIdx.x; k < g.n; k += blockDim.x) VL<V>::xa(g)[k] = VL<V>::xa(d)[k];
 }
 
 // Level 0's right-hand side is the CG residual r; the first pre-smoothing
@@ -520,6 +616,8 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
     __shared__ int s_coarse_ok;
     __shared__ double s_chol[kAmgCoarseMax * kAmgCoarseMax];   // block 0: coarsest factor
     __shared__ double s_cy[kAmgCoarseMax];
+    __shared__ AmgLevelDev s_lev[kAmgMaxLev];                     // block 0: shared-memory levels
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     const int t0 = threadIdx.x, step = blockDim.x;
     const AmgLevelDev &L0 = a.lev[0];
     const int N = L0.n;
@@ -551,7 +649,9 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
         }
         __syncthreads();
         if (threadIdx.x == 0) *(volatile int *)a.coarse_ok = s_coarse_ok;
+        if (a.shadow && a.L > 0) shadow_setup<V>(a, s_lev, s_dyn);
     }
+    const AmgLevelDev *blev = (a.shadow && a.L > 0) ? s_lev : a.lev;
 
     // ---- r = b - A x, norms
     if (ok) {
@@ -585,25 +685,29 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
                 // (the barrier before the first sweep of level 0 is the one
                 // that ended the previous phase)
                 if (l > 0 && !(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]),
+                phase_sweep<V>(a.lev, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]),
                                grid_rows(a.lev[l].n), t0, step);
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_restrict<V>(a, l, grid_rows(a.lev[l + 1].n), t0, step);
+                phase_restrict<V>(a.lev, l, grid_rows(a.lev[l + 1].n), t0, step);
             }
             if (!ok) break;
             if (a.L == 0) {
                 // a single level: the exact solve
-                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve<V>(a, s_chol, s_cy);
+                if (blockIdx.x == 0 && threadIdx.x < 32) coarse_solve<V>(a, a.lev, s_chol, s_cy);
             } else {
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                if (blockIdx.x == 0) block_levels_down_up<V>(a, s_chol, s_cy);
+                if (blockIdx.x == 0) {
+                    if (blev != a.lev) shadow_in<V>(a, blev);
+                    block_levels_down_up<V>(a, blev, s_chol, s_cy);
+                    if (blev != a.lev) shadow_out<V>(a, blev);
+                }
             }
             double v1[1] = {0.0};
             for (int l = min(a.G, a.L) - 1; l >= 0; --l) {
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_prolong_sweep<V>(a, l, grid_rows(a.lev[l].n), t0, step);
+                phase_prolong_sweep<V>(a.lev, l, grid_rows(a.lev[l].n), t0, step);
                 if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
-                phase_sweep<V>(a, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]),
+                phase_sweep<V>(a.lev, l, VL<V>::x(a.lev[l]), VL<V>::xa(a.lev[l]),
                                grid_rows(a.lev[l].n), t0, step);
             }
             if (!ok) break;
@@ -849,6 +953,35 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
     per_sm = std::min(per_sm, per_sm32);
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "multigrid CG kernel cannot be resident");
     h->grid = m->sm_count * std::min(per_sm, 2);
+    // block 0's shared-memory copy of the levels it runs (the layout of
+    // shadow_setup, FP64 sizes), if it fits without costing residency;
+    // FVGB_AMG_SHADOW=0 keeps those levels in global memory
+    if (L > 0) {
+        auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        size_t bytes = 0;
+        for (int l = G; l <= L; ++l) {
+            const size_t n = g[l].n, nsl = (n + 31) / 32;
+            std::vector<int32_t> sptr, scol, sedge;
+            graph_sell(g[l], sptr, scol, sedge);
+            const size_t slots = scol.size();
+            bytes += a16(8 * slots) + 5 * a16(8 * n) + a16(4 * (nsl + 1)) + a16(4 * slots);
+            if (l < L) bytes += a16(4 * n);
+            if (l > G) bytes += a16(4 * (n + 1)) + a16(4 * (size_t)g[l - 1].n);
+        }
+        const char *env = std::getenv("FVGB_AMG_SHADOW");
+        const bool allow = !(env && std::atoi(env) == 0);
+        if (allow && bytes <= (size_t)kAmgShadowMax) {
+            int p64 = 0, p32 = 0;
+            const int sb = (int)bytes;
+            if (cudaFuncSetAttribute(k_pcg_amg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
+                cudaFuncSetAttribute(k_pcg_amg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, k_pcg_amg<double>, kAmgBlock, sb) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, k_pcg_amg<float>, kAmgBlock, sb) == cudaSuccess &&
+                std::min(p64, p32) >= std::min(per_sm, 2))
+                h->shadow_bytes = sb;
+            (void)cudaGetLastError();
+        }
+    }
     *out = h;
     return FV_OK;
 }
@@ -880,6 +1013,7 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     a.o0 = pb.off;
     a.o0_sign = pb.off_sign;
     a.fp32 = pb.fp32;
+    a.shadow = h->shadow_bytes > 0 ? 1 : 0;
     a.b = pb.b;
     a.x = pb.x;
     a.r = h->r;
@@ -903,6 +1037,7 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kAmgBlock);
+    cfg.dynamicSmemBytes = (size_t)h->shadow_bytes;
     cfg.stream = m->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -93,6 +93,8 @@ struct KrylovWork {
     int block = 0;
     int cg_res_max = 0;      // dynamic shared memory the resident CG form may use (bytes)
     int mix_res_max = 0;     // the same for the resident mixed-precision CG form
+    int cgcg_res_max = 0;    // the same for the Chronopoulos-Gear mixed-precision form
+    int mixed_form = 2;      // mixed CG inner order: 0 textbook, 1 Chronopoulos-Gear, 2 by regime
     double *val = nullptr;   // SELL values (scaled copy for CG)
     double *val2 = nullptr;  // second SELL value buffer (BiCGStab input copy)
     double *dinv = nullptr;  // [N] (BiCGStab) / scaling s (CG)
@@ -100,6 +102,7 @@ struct KrylovWork {
     double *bv[9] = {};      // BiCGStab: r, rh, p, v, y(s), z, t ... per component [3N] each
     float *val32 = nullptr;      // FP32 scaled SELL values (mixed precision, lazily)
     float *f32[6] = {};          // FP32 inner vectors r, p, q, e, w, v [N]
+    float *f32p[2] = {};         // Chronopoulos-Gear form: s = A^ p, w = A^ r [N]
     double *partials = nullptr;  // [2][G][8]
     GridBar *bar = nullptr;
     DevSolveStats *stats = nullptr;  // [4] scratch for stand-alone calls

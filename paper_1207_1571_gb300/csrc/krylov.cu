@@ -27,6 +27,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdlib>
+#include <cstring>
 
 #include "fvgb_internal.h"
 #include "coop.cuh"
@@ -719,6 +720,342 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
     }
 }
 
+// ----------------------------- mixed precision, Chronopoulos-Gear order --
+//
+// The same method (FP32 deflated CG with reliable updates inside FP64 defect
+// correction) with the inner iterations in the order of Chronopoulos and
+// Gear (1989): the product of an iteration is w = A^ r^ of the new
+// residual, and with s = A^ p carried by the recurrence s = w + beta s the
+// sums the next iteration needs -- r^.r^, w.r^ and, for the deflation,
+// v.r^ -- are all formed with that product.  An iteration is then one
+// vector pass, a grid barrier (the product gathers the neighbours' new
+// residual) and one product pass ending in one grid sum: two
+// synchronisations against three for the textbook order (k_pcg_mixed).
+// (The fully pipelined order of Ghysels and Vanroose, one synchronisation
+// with z = A^ s carried as well, broke down in FP32 on these pressure
+// systems from 64^3 cells up, with or without replacing s and z at every
+// reliable update; this order converges like the textbook one.)
+//
+// With c = (v.r^)/mu the deflated direction p = r^ + beta p - c w_d (w_d =
+// D^1/2 1) has s = w + beta s - c v, and its curvature is
+// p.A^p = w.r^ - beta r^.r^ / alpha_prev - (v.r^) c (the identities
+// r^_k . r^_(k-1) = 0 and p_(k-1).A^p_k = 0).  After a reliable update the
+// residual is the refreshed one, for which those identities hold only
+// approximately, so that iteration takes its curvature from explicit sums
+// (r^.s and p.s of the kept direction).  FP64 keeps the true residual, the
+// stopping test, the solution and all cross-thread sums, as in k_pcg_mixed.
+
+struct CgcgArgs {
+    int N;
+    const int32_t *slice_ptr, *col;
+    const double *val;      // FP64 off-diagonals (unscaled), read only
+    float *val32;           // FP32 scaled off-diagonals (written in setup)
+    const double *diag, *b;
+    double *x, *s64, *r64, *a1;
+    float *r;                           // residual (global: gathered by neighbours)
+    float *p, *sv, *e, *w;              // row-local (shared memory in the resident form)
+    float *wd, *v;                      // deflation: w_d = D^1/2 1, v = A^ w_d
+    double *partA, *partB;
+    GridBar *bar;
+    long long spin;
+    double tol, reltol;
+    int maxit;
+    DevSolveStats *stats;
+};
+
+struct CgcgScalars {
+    double nb, nr0, nr, thresh, rho, ratio, alpha, beta, c, mu, inv_mu, shift;
+    double rel2, pred2;
+    int phase;       // 0 run, 1 converged, 2 iteration budget used, 3 breakdown, 4 zero rhs
+    int refresh;     // 1: refresh after this iteration, 2: refresh and restart p
+    int restart;     // no kept search direction (first pass or after a breakdown)
+    int bad;         // consecutive forced refreshes without progress
+    int deflate;
+};
+
+__device__ __forceinline__ float spmv32_gather(const CgcgArgs &a, const RowSpan &rs,
+                                               const float *__restrict__ src, float own)
+{
+    float acc = own;
+    if (rs.K <= 6) {
+        int c[6];
+        float v[6], x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) { c[k] = a.col[rs.e0 + 32 * k]; v[k] = a.val32[rs.e0 + 32 * k]; }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) x[k] = src[c[k]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < rs.K) acc = fmaf(v[k], x[k], acc);
+    } else {
+        for (int k = 0; k < rs.K; ++k) {
+            const int e = rs.e0 + 32 * k;
+            acc = fmaf(a.val32[e], src[a.col[e]], acc);
+        }
+    }
+    return acc;
+}
+
+// RES: p, s, e and w (read and written only by the thread owning the row)
+// live in the block's shared memory, 4 x chunk floats.
+template <bool RES>
+__global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed_cgcg(CgcgArgs a)
+{
+    __shared__ double buf[5][kCgBlock];
+    __shared__ double tot[5];
+    __shared__ CgcgScalars sc;
+    const int N = a.N;
+    const int nsl = (N + 31) >> 5;
+    const int chunk = ((nsl + gridDim.x - 1) / gridDim.x) * 32;
+    const int rb = blockIdx.x * chunk;
+    const int re = min(N, rb + chunk);
+    const int i0 = rb + threadIdx.x;
+    extern __shared__ float resc[];
+    const int o = RES ? rb : 0;
+    float *const pl = RES ? resc : a.p;
+    float *const sl = RES ? resc + chunk : a.sv;
+    float *const el = RES ? resc + 2 * chunk : a.e;
+    float *const wl = RES ? resc + 3 * chunk : a.w;
+    float *const rg = a.r;
+    unsigned gen = 0;
+    unsigned nred = 0;           // reductions so far: alternate partial buffers
+    bool ok = true;
+    int it = 0, outer = 0;
+#define CGCG_PART (((nred++) & 1u) ? a.partB : a.partA)
+
+    // S1: scaling
+    for (int i = i0; i < re; i += kCgBlock) a.s64[i] = 1.0 / sqrt(a.diag[i]);
+    ok = grid_sync(a.bar, gen, a.spin);
+    // S2: FP32 scaled matrix, A 1 (FP64), w_d = D^1/2 1, v = D^-1/2 A 1, mu = 1.A.1
+    if (ok) {
+        double v1[1] = {0.0};
+        for (int i = i0; i < re; i += kCgBlock) {
+            const RowSpan rs = row_span(a.slice_ptr, i);
+            const double si = a.s64[i];
+            double row = a.diag[i];
+            for (int k = 0; k < rs.K; ++k) {
+                const int e = rs.e0 + 32 * k;
+                const double v = a.val[e];
+                row += v;
+                a.val32[e] = (float)(v * si * a.s64[a.col[e]]);
+            }
+            a.a1[i] = row;
+            a.wd[i] = (float)(1.0 / si);
+            a.v[i] = (float)(si * row);
+            v1[0] += row;
+        }
+        ok = cg_grid_sum<1>(v1, CGCG_PART, a.bar, gen, a.spin, buf, tot);
+    }
+    if (threadIdx.x == 0) {
+        sc.phase = 0;
+        sc.alpha = sc.beta = sc.c = 0.0;
+        sc.restart = 1;
+        sc.bad = 0;
+        sc.refresh = 0;
+        sc.nr = 0.0;
+        sc.rho = 0.0;
+        sc.mu = tot[0];
+        sc.inv_mu = 1.0 / tot[0];
+        sc.deflate = (tot[0] > 0.0 && isfinite(tot[0])) ? 1 : 0;
+    }
+    __syncthreads();
+    while (ok) {
+        // R1: FP64 true residual from x; 1.r for the coarse correction
+        double v2[2] = {0.0, 0.0};     // ||b||^2, 1.r
+        for (int i = i0; i < re; i += kCgBlock) {
+            const RowSpan rs = row_span(a.slice_ptr, i);
+            double ax = a.diag[i] * a.x[i];
+            for (int k = 0; k < rs.K; ++k) {
+                const int e = rs.e0 + 32 * k;
+                ax += a.val[e] * a.x[a.col[e]];
+            }
+            const double bi = a.b[i];
+            const double ri = bi - ax;
+            a.r64[i] = ri;
+            v2[0] += bi * bi;
+            v2[1] += ri;
+        }
+        if (!(ok = cg_grid_sum<2>(v2, CGCG_PART, a.bar, gen, a.spin, buf, tot))) break;
+        if (threadIdx.x == 0) {
+            if (outer == 0) sc.nb = sqrt(tot[0]);
+            sc.shift = sc.deflate ? tot[1] / sc.mu : 0.0;
+        }
+        __syncthreads();
+        // R2: coarse correction x += shift, FP32 scaled residual, e = 0;
+        // ||r||^2 in FP64
+        {
+            const double sh = sc.shift;
+            double v1[1] = {0.0};
+            for (int i = i0; i < re; i += kCgBlock) {
+                const double ri = a.r64[i] - sh * a.a1[i];
+                a.x[i] += sh;
+                rg[i] = (float)(a.s64[i] * ri);
+                el[i - o] = 0.0f;
+                v1[0] += ri * ri;
+            }
+            if (!(ok = cg_grid_sum<1>(v1, CGCG_PART, a.bar, gen, a.spin, buf, tot))) break;
+        }
+        if (threadIdx.x == 0) {
+            const double prev = sc.nr;
+            sc.nr = sqrt(tot[0]);
+            if (outer == 0) {
+                sc.nr0 = sc.nr;
+                sc.thresh = fmax(a.tol * sc.nb, a.reltol * sc.nr0);
+                if (sc.nb == 0.0) sc.phase = 4;
+            } else if (sc.refresh == 2) {
+                sc.bad = (sc.nr >= prev) ? sc.bad + 1 : 0;
+                if (sc.bad >= 2) sc.phase = 3;
+            }
+            if (sc.phase == 0) {
+                if (!isfinite(sc.nr)) sc.phase = 3;
+                else if (sc.nr <= sc.thresh) sc.phase = 1;
+                else if (it >= a.maxit) sc.phase = 2;
+            }
+        }
+        __syncthreads();
+        ++outer;
+        if (sc.phase != 0) break;
+        // R3: w = A^ r^; the sums that start the iterations: r^.r^, w.r^, v.r^
+        // and, for a kept direction, r^.s and p.s (else p = s = 0)
+        {
+            const bool keep = !sc.restart;
+            float g = 0.0f, d = 0.0f, ep = 0.0f, sg = 0.0f, pp = 0.0f;
+            for (int i = i0; i < re; i += kCgBlock) {
+                const RowSpan rs = row_span(a.slice_ptr, i);
+                const float ri = rg[i];
+                const float wi = spmv32_gather(a, rs, rg, ri);
+                wl[i - o] = wi;
+                g = fmaf(ri, ri, g);
+                d = fmaf(wi, ri, d);
+                ep = fmaf(a.v[i], ri, ep);
+                if (keep) {
+                    const float si = sl[i - o];
+                    sg = fmaf(ri, si, sg);
+                    pp = fmaf(pl[i - o], si, pp);
+                } else {
+                    pl[i - o] = 0.0f;
+                    sl[i - o] = 0.0f;
+                }
+            }
+            double v5[5] = {(double)g, (double)d, (double)ep, (double)sg, (double)pp};
+            if (!(ok = cg_grid_sum<5>(v5, CGCG_PART, a.bar, gen, a.spin, buf, tot))) break;
+        }
+        if (threadIdx.x == 0) {
+            const double gam = tot[0], del = tot[1], eps = tot[2];
+            const double c = sc.deflate ? eps * sc.inv_mu : 0.0;
+            double beta = (!sc.restart && sc.rho > 0.0) ? gam / sc.rho : 0.0;
+            // curvature of the new direction from explicit sums
+            double den = del + beta * (2.0 * tot[3] + beta * tot[4]) - eps * c;
+            if (!(den > 0.0) && beta != 0.0) {
+                // drop the kept direction (p = s = 0 is not set here: beta = 0
+                // multiplies them, and they are finite)
+                beta = 0.0;
+                den = del - eps * c;
+            }
+            if (!(den > 0.0) || !isfinite(den) || !isfinite(gam)) {
+                sc.phase = 3;
+            } else {
+                sc.beta = beta;
+                sc.c = c;
+                sc.alpha = gam / den;
+                sc.rho = gam;
+                sc.ratio = gam > 0.0 ? sc.nr / sqrt(gam) : 0.0;
+                sc.rel2 = kReliable * kReliable * gam;
+                sc.pred2 = sc.ratio > 0.0 ? (sc.thresh / sc.ratio) * (sc.thresh / sc.ratio) : INFINITY;
+                sc.refresh = 0;
+                sc.restart = 0;
+            }
+        }
+        __syncthreads();
+        if (sc.phase != 0) break;
+        // inner iterations: a vector pass, a barrier, the product with its sum
+        while (true) {
+            ++it;
+            {
+                const float al = (float)sc.alpha, be = (float)sc.beta, cc = (float)sc.c;
+                float *__restrict__ pv = pl;
+                float *__restrict__ sv = sl;
+                float *__restrict__ ev = el;
+                float *__restrict__ rv = rg;
+                const float *__restrict__ wv = wl;
+#pragma unroll 2
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const float po = pv[i - o], so = sv[i - o], eo = ev[i - o];
+                    const float ri = rv[i], wi = wv[i - o], wdi = a.wd[i], vi = a.v[i];
+                    const float pi = fmaf(-cc, wdi, fmaf(be, po, ri));
+                    const float si = fmaf(-cc, vi, fmaf(be, so, wi));
+                    pv[i - o] = pi;
+                    sv[i - o] = si;
+                    ev[i - o] = fmaf(al, pi, eo);
+                    rv[i] = fmaf(-al, si, ri);
+                }
+            }
+            if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+            float g = 0.0f, d = 0.0f, ep = 0.0f;
+            {
+                float *__restrict__ wv = wl;
+#pragma unroll 2
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const RowSpan rs = row_span(a.slice_ptr, i);
+                    const float ri = rg[i];
+                    const float wi = spmv32_gather(a, rs, rg, ri);
+                    wv[i - o] = wi;
+                    g = fmaf(ri, ri, g);
+                    d = fmaf(wi, ri, d);
+                    ep = fmaf(a.v[i], ri, ep);
+                }
+            }
+            double v3[3] = {(double)g, (double)d, (double)ep};
+            if (!(ok = cg_grid_sum<3>(v3, CGCG_PART, a.bar, gen, a.spin, buf, tot))) break;
+            if (threadIdx.x == 0) {
+                const double gam = tot[0], del = tot[1], eps = tot[2];
+                if (!isfinite(gam) || !isfinite(del)) {
+                    sc.refresh = 2;
+                } else if (gam <= sc.rel2 || gam <= sc.pred2 || it >= a.maxit) {
+                    // refresh; sc.rho keeps r^.r^ of the previous iteration so
+                    // that beta can be formed with the refreshed residual
+                    sc.refresh = 1;
+                } else {
+                    const double beta = gam / sc.rho;
+                    const double c = sc.deflate ? eps * sc.inv_mu : 0.0;
+                    const double den = del - beta * gam / sc.alpha - eps * c;
+                    if (!(den > 0.0) || !isfinite(den)) {
+                        sc.refresh = 2;
+                    } else {
+                        sc.beta = beta;
+                        sc.c = c;
+                        sc.alpha = gam / den;
+                        sc.rho = gam;
+                    }
+                }
+            }
+            __syncthreads();
+            if (sc.refresh) break;
+        }
+        if (!ok) break;
+        // fold the FP32 correction into the FP64 solution
+        for (int i = i0; i < re; i += kCgBlock) a.x[i] += a.s64[i] * (double)el[i - o];
+        if (threadIdx.x == 0 && sc.refresh == 2) sc.restart = 1;
+        __syncthreads();
+        if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
+    }
+#undef CGCG_PART
+    if (ok && sc.phase == 4)
+        for (int i = i0; i < re; i += kCgBlock) a.x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int ph = sc.phase;
+        a.stats->iters = it;
+        a.stats->status = !ok ? FV_E_TIMEOUT
+                        : ph == 3 ? FV_E_DIVERGED : ph == 2 ? FV_E_NOT_CONVERGED : FV_OK;
+        const bool zero = ph == 4;
+        a.stats->res0 = zero ? 0.0 : sc.nr0 / sc.nb;
+        a.stats->res = zero ? 0.0 : sc.nr / sc.nb;
+        a.stats->outer = outer;
+    }
+}
+
 // ------------------------------------------------------------ BiCGStab --
 
 struct BicgArgs {
@@ -970,7 +1307,18 @@ fv_status krylov_setup(fv_mesh *m)
         const bool allow = !(env && std::atoi(env) == 0);
         w.cg_res_max = resident_room((const void *)k_pcg<true>, allow);
         w.mix_res_max = resident_room((const void *)k_pcg_mixed<true>, allow);
+        w.cgcg_res_max = resident_room((const void *)k_pcg_mixed_cgcg<true>, allow);
+        // order of the mixed-precision inner iterations: by default the
+        // Chronopoulos-Gear order where its row vectors fit in shared
+        // memory (synchronisation-bound there: 2 instead of 3 per
+        // iteration), the textbook order otherwise (bandwidth-bound there,
+        // and it moves fewer bytes); FVGB_MIXED_CG=classic or cgcg forces one
+        const char *form = std::getenv("FVGB_MIXED_CG");
+        w.mixed_form = !form ? 2 : std::strcmp(form, "classic") == 0 ? 0
+                     : std::strcmp(form, "cgcg") == 0 ? 1 : 2;
     }
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed_cgcg<false>, kCgBlock, 0));
+    FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel (Chronopoulos-Gear order) cannot be resident");
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mixed<false>, kCgBlock, 0));
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel cannot be resident");
     w.Gcg = m->sm_count;
@@ -1040,6 +1388,50 @@ fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb)
         for (int k = 0; k < 6; ++k)
             if ((st = ar.alloc_n(&w.f32[k], (size_t)m->N)) != FV_OK) return st;
     }
+    const int G = grid_for(m->N, kCgBlock, w.Gcg);
+    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
+    const bool cgcg_fits = (size_t)4 * sizeof(float) * cg_chunk(m->N, G) <= (size_t)w.cgcg_res_max;
+    if (w.mixed_form == 1 || (w.mixed_form == 2 && cgcg_fits)) {
+        if (!w.f32p[0]) {
+            DeviceArena &ar = mm->arena;
+            fv_status st;
+            for (int k = 0; k < 2; ++k)
+                if ((st = ar.alloc_n(&w.f32p[k], (size_t)m->N)) != FV_OK) return st;
+        }
+        CgcgArgs a;
+        a.N = m->N;
+        a.slice_ptr = m->slice_ptr;
+        a.col = m->col;
+        a.val = pb.val;
+        a.val32 = w.val32;
+        a.diag = pb.diag;
+        a.b = pb.b;
+        a.x = pb.x;
+        a.s64 = w.dinv;
+        a.r64 = w.r;
+        a.a1 = w.y;
+        a.r = w.f32[0];
+        a.p = w.f32[1];
+        a.e = w.f32[3];
+        a.wd = w.f32[4];
+        a.v = w.f32[5];
+        a.sv = w.f32p[0];
+        a.w = w.f32p[1];
+        a.partA = w.partials;
+        a.partB = w.partials + (size_t)gp * kParts;
+        a.bar = w.bar;
+        a.spin = g_spin_limit;
+        a.tol = pb.tol;
+        a.reltol = pb.reltol;
+        a.maxit = pb.maxit;
+        a.stats = pb.stats;
+        FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
+        void *args[] = {&a};
+        const size_t res = (size_t)4 * sizeof(float) * cg_chunk(m->N, G);
+        if (res <= (size_t)w.cgcg_res_max)
+            return coop_launch((const void *)k_pcg_mixed_cgcg<true>, G, kCgBlock, args, m->stream, res);
+        return coop_launch((const void *)k_pcg_mixed_cgcg<false>, G, kCgBlock, args, m->stream);
+    }
     MixArgs a;
     a.N = m->N;
     a.slice_ptr = m->slice_ptr;
@@ -1058,7 +1450,6 @@ fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb)
     a.e = w.f32[3];
     a.w = w.f32[4];
     a.v = w.f32[5];
-    const int gp = w.G > w.Gcg ? w.G : w.Gcg;
     a.partA = w.partials;
     a.partB = w.partials + (size_t)gp * kParts;
     a.bar = w.bar;
@@ -1069,7 +1460,6 @@ fv_status launch_pcg_mixed(const fv_mesh *m, const MixedProblem &pb)
     a.stats = pb.stats;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
     void *args[] = {&a};
-    const int G = grid_for(m->N, kCgBlock, w.Gcg);
     const size_t res = (size_t)5 * sizeof(float) * cg_chunk(m->N, G);
     if (res <= (size_t)w.mix_res_max)
         return coop_launch((const void *)k_pcg_mixed<true>, G, kCgBlock, args, m->stream, res);

@@ -46,13 +46,14 @@ def test_two_rank_max_and_barrier():
 
 def test_reference_arm_json_line():
     """`bench.py --impl reference` (the oracle arm) prints one JSON line with
-    the contract's keys, on the host cores, without a GPU."""
+    the contract's keys, on the host cores, without a GPU (here on the 40^3
+    cavity; the arm times the first steps of the workload it is given)."""
     import json
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, cwd=root,
+                        "--steps", "1", "--warmup", "0", "--workload", "cavity3d_40"], capture_output=True, text=True, cwd=root,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -62,5 +63,6 @@ def test_reference_arm_json_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["config"]["same_config"] is True and d["config"]["cells"] == 40 ** 3
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]

@@ -220,6 +220,32 @@ def test_piso_with_amg_graph_replay(P):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_amg_shared_memory_levels_identical(P, monkeypatch, precision):
+    """Block 0 runs the levels of up to 256 rows from a shared-memory copy
+    (FVGB_AMG_SHADOW=0 keeps them in global memory); the arithmetic and its
+    order are the same, so the results are the same bits, for the FP64 and
+    the FP32 cycle."""
+    m = mg.permute_cells(mg.cavity3d(40), mg.random_permutation(40 ** 3, 3))
+    prec = P.FV_PREC_FP64 if precision == "fp64" else P.FV_PREC_MIXED
+    out = []
+    for env in ("1", "0"):
+        monkeypatch.setenv("FVGB_AMG_SHADOW", env)
+        mesh = P.Mesh(m, renumber=True)
+        case = P.Case(mesh, 0.01, prec)
+        case.set_pressure_solver(P.FV_PSOLVER_AMG)
+        its = []
+        for _ in range(3):
+            s = case.piso_step(0.005, 2, p_ref_cell=m.corner_cell)
+            assert s["status"] == 0
+            its.append([int(k) for k in s["iters"]])
+        out.append((case.get_fields_host(), its))
+    (fa, ia), (fb, ib) = out
+    assert ia == ib
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+
+
 def test_tp_reduced_with_amg(P):
     m = mg.tp_channel(320, 30)
     dt = 1e-4

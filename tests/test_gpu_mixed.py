@@ -1,5 +1,8 @@
 """Mixed-precision pressure solve (FP32 inner Jacobi-CG inside FP64 defect
-correction) against the FP64 oracle.
+correction) against the FP64 oracle, with the inner iterations in both
+orders: Chronopoulos-Gear (two synchronisations per iteration, the
+default) and textbook (FVGB_MIXED_CG=classic, read when a mesh is
+created).
 
 The gate is the true FP64 residual: ||b - A x|| <= tol ||b||, evaluated here
 with the oracle's own LDU product.  The error of every field against the
@@ -23,6 +26,12 @@ def P():
     import paper_1207_1571_gb300 as P
     P.load()
     return P
+
+
+@pytest.fixture(autouse=True, params=["cgcg", "classic"])
+def form(request, monkeypatch):
+    monkeypatch.setenv("FVGB_MIXED_CG", request.param)
+    return request.param
 
 
 def rel(a, b):

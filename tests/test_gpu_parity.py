@@ -66,6 +66,7 @@ def assert_iters(s, so):
 @pytest.mark.parametrize("maker", [
     lambda: mg.permute_cells(mg.cavity3d(10), mg.random_permutation(1000, 1234)),
     lambda: mg.tet_box(3, 3, 5, jitter=0.1),
+    lambda: mg.mixed_box(4, 5, 3, jitter=0.15),
     lambda: mg.cavity2d(20)])
 def test_mesh_addressing_bit_exact(P, maker):
     m = maker()
@@ -303,6 +304,40 @@ def test_piso_tets_nonorth_correctors(P, nn):
     assert_fields(case, oc)
 
 
+@pytest.mark.parametrize("nn", [0, 1])
+def test_piso_mixed_element_cavity(P, nn):
+    """The lid-driven cavity on a jittered mixed mesh of hexahedra, prisms and
+    pyramids (non-planar faces, non-orthogonal everywhere), with and without
+    a non-orthogonal corrector: 5 PISO steps in lockstep with the oracle."""
+    m = mg.mixed_cavity3d(8, jitter=0.12, seed=9)
+    mesh, case, om, oc = both(P, m, 0.02)
+    assert mesh.info()["nonorth"]
+    for step in range(5):
+        s = case.piso_step(0.01, 2, p_ref_cell=m.corner_cell, n_nonorth=nn)
+        so = oc.piso_step(0.01, 2, p_ref_cell=m.corner_cell, n_nonorth=nn)
+        assert s["status"] == 0
+        assert_iters(s, so)
+    assert_fields(case, oc)
+
+
+def test_simple_mixed_element_duct(P):
+    """SIMPLE on a jittered mixed-element duct with an inlet profile and an
+    outlet, one non-orthogonal corrector per iteration."""
+    m = mg.mixed_duct(4, 8, jitter=0.1, seed=4)
+    F = m.n_internal_faces
+    inl = m.patches[m.patch("inlet")]
+    xy = m.Cf[:2, F + inl.start:F + inl.start + inl.size]
+    prof = mg.duct_inlet_profile(xy)
+    mesh, case, om, oc = both(P, m, 0.05)
+    for c in (case, oc):
+        c.set_patch_faces(m.patch("inlet"), np.stack([0 * prof, 0 * prof, prof]))
+    for it in range(10):
+        s = case.simple_iter(0.7, 0.3, n_nonorth=1)
+        so = oc.simple_iter(0.7, 0.3, n_nonorth=1)
+        assert_iters(s, so)
+    assert_fields(case, oc)
+
+
 def test_simple_tets_nonorth_correctors(P):
     m = mg.duct_tets(3, 6)
     F = m.n_internal_faces
@@ -398,15 +433,17 @@ def test_graph_replay_and_determinism(P):
     assert sb["status"] == 0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_classic"])
 def test_cg_resident_and_global_forms_identical(P, monkeypatch, precision):
     """The CG keeps its row-local vectors (FP64: r^, q, y; mixed precision:
-    the FP32 r^, q, e, w, v) in shared memory when a block's rows fit (meshes
-    up to about 1.2M cells on GB300) and in global memory otherwise; both
+    the FP32 r^, q, e, w, v of the textbook order, p, s, e, w of the
+    Chronopoulos-Gear order) in shared memory when a block's rows fit (meshes up to
+    about 1.2M cells on GB300) and in global memory otherwise; both
     forms do the same arithmetic in the same order, so a mesh created with
     FVGB_CG_RESIDENT=0 (global forms only) gives the same bits."""
     m = mg.permute_cells(mg.cavity3d(24), mg.random_permutation(24 ** 3, 5))
     prec = P.FV_PREC_FP64 if precision == "fp64" else P.FV_PREC_MIXED
+    monkeypatch.setenv("FVGB_MIXED_CG", "classic" if precision == "mixed_classic" else "cgcg")
     out = []
     for env in ("1", "0"):
         monkeypatch.setenv("FVGB_CG_RESIDENT", env)
