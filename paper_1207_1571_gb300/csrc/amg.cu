@@ -165,7 +165,9 @@ struct AmgData {
     int L = 0;                // index of the coarsest level
     int G = 1;                // levels 0..G-1 run over the whole grid
     int grid = 0;             // cooperative grid size
-    int shadow_bytes = 0;     // dynamic shared memory of block 0's copy of levels G..L (0: none)
+    int dyn_bytes = 0;        // dynamic shared memory of the solve kernel
+    int shadow = 0;           // block 0 keeps levels G..L in shared memory
+    int lev_table_bytes = 0;
     int n[kAmgMaxLev] = {}, ne[kAmgMaxLev] = {};
     AmgLevelDev *lev = nullptr;      // device copy of the level table
     int *coarse_ok = nullptr;
@@ -189,6 +191,7 @@ struct AmgArgs {
     double o0_sign;            // o = o0_sign * o0[f] (-1 when o0 holds the positive a_f)
     int fp32;                  // the V-cycle in FP32 (mixed precision)
     int shadow;                // block 0 keeps levels G..L in shared memory
+    int lev_table_bytes;       // room of the shared-memory level table (16-byte multiple)
     const double *b;
     double *x, *r, *z, *p, *q;
     double *partA, *partB;
@@ -614,10 +617,16 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
     __shared__ double tot[2];
     __shared__ AmgScal sc;
     __shared__ int s_coarse_ok;
-    __shared__ double s_chol[kAmgCoarseMax * kAmgCoarseMax];   // block 0: coarsest factor
-    __shared__ double s_cy[kAmgCoarseMax];
-    __shared__ AmgLevelDev s_lev[kAmgMaxLev];                     // block 0: shared-memory levels
+    // dynamic shared memory, used by block 0 only (every block holds it, so
+    // it is sized to the hierarchy: shared memory a block holds is L1 cache
+    // its SM does not have): the coarsest factor, the triangular solves'
+    // vector, and with the level copy the level table and the levels' data
     extern __shared__ __align__(16) unsigned char s_dyn[];
+    const int nc16 = (a.nc * a.nc * 8 + 15) & ~15, nv16 = (a.nc * 8 + 15) & ~15;
+    double *const s_chol = reinterpret_cast<double *>(s_dyn);
+    double *const s_cy = reinterpret_cast<double *>(s_dyn + nc16);
+    AmgLevelDev *const s_lev = reinterpret_cast<AmgLevelDev *>(s_dyn + nc16 + nv16);
+    unsigned char *const s_levdata = s_dyn + nc16 + nv16 + a.lev_table_bytes;
     const int t0 = threadIdx.x, step = blockDim.x;
     const AmgLevelDev &L0 = a.lev[0];
     const int N = L0.n;
@@ -649,7 +658,7 @@ __global__ void __launch_bounds__(kAmgBlock) k_pcg_amg(AmgArgs a)
         }
         __syncthreads();
         if (threadIdx.x == 0) *(volatile int *)a.coarse_ok = s_coarse_ok;
-        if (a.shadow && a.L > 0) shadow_setup<V>(a, s_lev, s_dyn);
+        if (a.shadow && a.L > 0) shadow_setup<V>(a, s_lev, s_levdata);
     }
     const AmgLevelDev *blev = (a.shadow && a.L > 0) ? s_lev : a.lev;
 
@@ -953,13 +962,17 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
     per_sm = std::min(per_sm, per_sm32);
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "multigrid CG kernel cannot be resident");
     h->grid = m->sm_count * std::min(per_sm, 2);
-    // block 0's shared-memory copy of the levels it runs (the layout of
-    // shadow_setup, FP64 sizes), if it fits without costing residency;
-    // FVGB_AMG_SHADOW=0 keeps those levels in global memory
-    if (L > 0) {
+    // dynamic shared memory: the coarsest factor and vector, and block 0's
+    // copy of the levels it runs (the layout of shadow_setup, FP64 sizes) if
+    // that keeps two blocks per SM; FVGB_AMG_SHADOW=0 keeps those levels in
+    // global memory
+    {
         auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        const size_t nc = g[L].n;
+        const size_t base = a16(8 * nc * nc) + a16(8 * nc);
+        const size_t table = a16(sizeof(AmgLevelDev) * (L + 1));
         size_t bytes = 0;
-        for (int l = G; l <= L; ++l) {
+        for (int l = G; l <= L && L > 0; ++l) {
             const size_t n = g[l].n, nsl = (n + 31) / 32;
             std::vector<int32_t> sptr, scol, sedge;
             graph_sell(g[l], sptr, scol, sedge);
@@ -969,17 +982,26 @@ fv_status amg_build(fv_mesh *m, AmgData **out)
             if (l > G) bytes += a16(4 * (n + 1)) + a16(4 * (size_t)g[l - 1].n);
         }
         const char *env = std::getenv("FVGB_AMG_SHADOW");
-        const bool allow = !(env && std::atoi(env) == 0);
-        if (allow && bytes <= (size_t)kAmgShadowMax) {
+        const bool want = !(env && std::atoi(env) == 0);
+        auto fits = [&](size_t dyn) {
             int p64 = 0, p32 = 0;
-            const int sb = (int)bytes;
-            if (cudaFuncSetAttribute(k_pcg_amg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
-                cudaFuncSetAttribute(k_pcg_amg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, k_pcg_amg<double>, kAmgBlock, sb) == cudaSuccess &&
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, k_pcg_amg<float>, kAmgBlock, sb) == cudaSuccess &&
-                std::min(p64, p32) >= std::min(per_sm, 2))
-                h->shadow_bytes = sb;
+            const int sb = (int)dyn;
+            bool ok = cudaFuncSetAttribute(k_pcg_amg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
+                      cudaFuncSetAttribute(k_pcg_amg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
+                      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, k_pcg_amg<double>, kAmgBlock, sb) == cudaSuccess &&
+                      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, k_pcg_amg<float>, kAmgBlock, sb) == cudaSuccess;
             (void)cudaGetLastError();
+            return ok ? std::min(p64, p32) : 0;
+        };
+        h->lev_table_bytes = (int)table;
+        if (want && L > 0 && bytes <= (size_t)kAmgShadowMax && fits(base + table + bytes) >= std::min(per_sm, 2)) {
+            h->shadow = 1;
+            h->dyn_bytes = (int)(base + table + bytes);
+        } else {
+            h->dyn_bytes = (int)(base + table);
+            const int p = fits(h->dyn_bytes);
+            FV_CHECK(p >= 1, FV_E_CUDA, "multigrid CG kernel cannot be resident");
+            h->grid = m->sm_count * std::min(p, 2);
         }
     }
     *out = h;
@@ -1013,7 +1035,8 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     a.o0 = pb.off;
     a.o0_sign = pb.off_sign;
     a.fp32 = pb.fp32;
-    a.shadow = h->shadow_bytes > 0 ? 1 : 0;
+    a.shadow = h->shadow;
+    a.lev_table_bytes = h->lev_table_bytes;
     a.b = pb.b;
     a.x = pb.x;
     a.r = h->r;
@@ -1037,7 +1060,7 @@ fv_status launch_pcg_amg(const fv_mesh *m, const AmgProblem &pb)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kAmgBlock);
-    cfg.dynamicSmemBytes = (size_t)h->shadow_bytes;
+    cfg.dynamicSmemBytes = (size_t)h->dyn_bytes;
     cfg.stream = m->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
