@@ -12,7 +12,12 @@ configurations, tests/test_gpu_zz_full_configs.py and test_gpu_zz_full8m.py).
 * 8M-cell cavity (200^3; nu 0.01, dt 0.001): all 20 PISO steps, FP64 and
   mixed precision, each against the FP64 oracle; the FP64 run within 1e-9
   of the oracle, the mixed run's per-field error reported (``-rA``) and
-  bounded by the 1e-6 solver tolerance's reach."""
+  bounded by the 1e-6 solver tolerance's reach.
+* the batch of 256 cavities (seed 7): all 200 steps, every case against its
+  own oracle run (one sequential oracle per host thread), strict where the
+  case's iteration counts agree within 1 and its fields within 1e-9, else
+  held to the case's own oracle envelope."""
+import concurrent.futures as cf
 import os
 import time
 
@@ -21,7 +26,7 @@ import pytest
 
 import meshgen as mg
 import oracle as O
-from parity_util import (field_errors, oracle_spread, assert_errors_within,
+from parity_util import (TOL, field_errors, oracle_spread, assert_errors_within,
                          assert_iters_where_well_conditioned)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow,
@@ -83,3 +88,63 @@ def test_cavity_200_cubed_all_20_steps_fp64_and_mixed(P):
     assert worst_its <= 1
     assert_errors_within(e64)
     assert emx["u"] < 1e-5 and emx["phi"] < 1e-5 and emx["p_meanfree"] < 1e-4, emx
+
+
+def _oracle_batch_case(args):
+    """One case's oracle run; with eps > 0 from a rest state perturbed by an
+    eps-sized random velocity (the oracle's own rounding sensitivity)."""
+    om, m, nu, ref, nsteps, eps, seed = args
+    oc = O.Case(om, nu)
+    if eps > 0:
+        u = np.zeros((3, m.n_cells))
+        u[:2] = eps * np.random.default_rng(seed).standard_normal((2, m.n_cells))
+        oc.set_fields(u, np.zeros(m.n_cells), np.zeros(m.n_faces))
+    its = [np.array(oc.piso_step(0.002, 2, p_ref_cell=ref)["iters"]) for _ in range(nsteps)]
+    return np.array(its), oc.get_fields()
+
+
+def test_batch_all_256_cases_all_200_steps(P):
+    nsteps = 200
+    spec = mg.batch_cases(256, 7)
+    ms = [mg.cavity2d(n) for n, _ in spec]
+    nus = [nu for _, nu in spec]
+    refs = [m.corner_cell for m in ms]
+    bt = P.Batch(ms, nus, refs)
+    gpu_its = [[] for _ in ms]
+    for _ in range(nsteps):
+        st = bt.piso_step(0.002, 2)
+        for k in range(len(ms)):
+            assert st[k]["status"] == 0, (k, st[k])
+            gpu_its[k].append(np.array(st[k]["iters"]))
+    gpu = [bt.get_fields(k) for k in range(len(ms))]
+    # oracle meshes in this thread (the renumbering is not reentrant), the
+    # case runs over the host cores
+    oms = [O.Mesh(m, renumber=True) for m in ms]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        res = list(ex.map(_oracle_batch_case, [(om, m, nu, r, nsteps, 0.0, 0)
+                                               for om, m, nu, r in zip(oms, ms, nus, refs)]))
+        loose = []
+        worst = {q: 0.0 for q in ("u", "phi", "p_meanfree", "p_mean")}
+        for k, (its_o, fo) in enumerate(res):
+            errs = field_errors(gpu[k], fo)
+            for q in worst:
+                worst[q] = max(worst[q], errs[q])
+            if not (np.abs(np.array(gpu_its[k]) - its_o).max() <= 1
+                    and all(errs[q] <= TOL for q in worst)):
+                loose.append(k)
+        # the cases whose stopping iterations are rounding-decided: against
+        # their own oracle envelope (two runs from 1e-15-perturbed rest states)
+        pert = list(ex.map(_oracle_batch_case, [(oms[k], ms[k], nus[k], refs[k], nsteps, 1e-15, sd)
+                                                for k in loose for sd in (1, 2)]))
+    for j, k in enumerate(loose):
+        its0, f0 = res[k]
+        its_p = [pert[2 * j][0], pert[2 * j + 1][0]]
+        spread = {}
+        for its, f in (pert[2 * j], pert[2 * j + 1]):
+            for q, v in field_errors(f, f0).items():
+                spread[q] = max(spread.get(q, 0.0), v)
+        assert_iters_where_well_conditioned(gpu_its[k], its0, its_p)
+        assert_errors_within(field_errors(gpu[k], f0), spread)
+    print(f"\nbatch of 256 cavities, {nsteps} steps: worst errors {worst}; {len(loose)} cases "
+          f"held to their oracle envelope; oracle {time.perf_counter() - t0:.0f} s")
