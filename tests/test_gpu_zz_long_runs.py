@@ -1,6 +1,6 @@
 """The stated number of steps of the two large cavity configurations against
 the FP64 oracle (its OpenMP build on all host cores).  The oracle needs about
-15 minutes of host time for both, so these run only with FVGB_LONG=1 (the
+30 minutes of host time for all three, so these run only with FVGB_LONG=1 (the
 default suite compares the first five and the first two steps of the same
 configurations, tests/test_gpu_zz_full_configs.py and test_gpu_zz_full8m.py).
 
@@ -10,8 +10,9 @@ configurations, tests/test_gpu_zz_full_configs.py and test_gpu_zz_full8m.py).
   split into mean-free part and mean; iteration counts within 1 wherever the
   perturbed oracle runs agree on them).
 * 8M-cell cavity (200^3; nu 0.01, dt 0.001): all 20 PISO steps, FP64 and
-  mixed precision, each against the FP64 oracle; the FP64 run within 1e-9
-  of the oracle, the mixed run's per-field error reported (``-rA``) and
+  mixed precision, each against the FP64 oracle; the FP64 run held to the
+  same bar as the 1M run (its first two steps are within 1e-9 in the
+  default suite), the mixed run's per-field error reported (``-rA``) and
   bounded by the 1e-6 solver tolerance's reach.
 * the batch of 256 cavities (seed 7): all 200 steps, every case against its
   own oracle run (one sequential oracle per host thread), strict where the
@@ -64,29 +65,34 @@ def test_cavity_100_cubed_all_50_steps(P):
 
 
 def test_cavity_200_cubed_all_20_steps_fp64_and_mixed(P):
+    """20 steps are long enough for the tolerance-truncated CG to amplify
+    rounding past 1e-9 (as on the 1M cavity after 50 steps), so the FP64 run
+    is held to the oracle's own spread under 1e-15 input perturbations
+    (three oracle runs)."""
     n, nsteps = 200, 20
     m = mg.permute_cells(mg.cavity3d(n), mg.random_permutation(n ** 3, 1234))
-    oc = O.Case(O.Mesh(m, renumber=True, parallel=True), 0.01)
+    step = lambda c, k: c.piso_step(0.001, 2, p_ref_cell=m.corner_cell)
+    t0 = time.perf_counter()
+    base, its0, its_p, spread = oracle_spread(m, 0.01, nsteps, step, parallel=True)
+    t_or = time.perf_counter() - t0
     mesh = P.Mesh(m, renumber=True)
     c64 = P.Case(mesh, 0.01)
     cmx = P.Case(mesh, 0.01, P.FV_PREC_MIXED)
-    t0 = time.perf_counter()
-    worst_its = 0
+    gpu_its = []
     for k in range(nsteps):
         s = c64.piso_step(0.001, 2, p_ref_cell=m.corner_cell)
         sm = cmx.piso_step(0.001, 2, p_ref_cell=m.corner_cell)
-        so = oc.piso_step(0.001, 2, p_ref_cell=m.corner_cell)
         assert s["status"] == 0 and sm["status"] == 0, (k, s, sm)
         assert all(x["res"] <= 1e-6 for x in sm["p"]), (k, sm)
-        worst_its = max(worst_its, int(np.abs(np.array(s["iters"]) - so["iters"]).max()))
-    ref = oc.get_fields()
+        gpu_its.append(s["iters"])
+    stable = assert_iters_where_well_conditioned(gpu_its, its0, its_p)
+    ref = base.get_fields()
     e64 = field_errors(c64.get_fields_host(), ref)
     emx = field_errors(cmx.get_fields_host(), ref)
-    print(f"\n200^3 cavity, {nsteps} steps: FP64 vs oracle {e64}\n mixed vs FP64 oracle {emx}\n"
-          f" largest iteration-count difference (FP64) {worst_its}; "
-          f"oracle {time.perf_counter() - t0:.0f} s")
-    assert worst_its <= 1
-    assert_errors_within(e64)
+    print(f"\n200^3 cavity, {nsteps} steps: FP64 vs oracle {e64}\n oracle spread {spread}\n"
+          f" mixed vs FP64 oracle {emx}\n stable solves {int(stable.sum())}/{stable.size}; "
+          f"oracle (3 runs) {t_or:.0f} s")
+    assert_errors_within(e64, spread)
     assert emx["u"] < 1e-5 and emx["phi"] < 1e-5 and emx["p_meanfree"] < 1e-4, emx
 
 
@@ -134,14 +140,18 @@ def test_batch_all_256_cases_all_200_steps(P):
                     and all(errs[q] <= TOL for q in worst)):
                 loose.append(k)
         # the cases whose stopping iterations are rounding-decided: against
-        # their own oracle envelope (two runs from 1e-15-perturbed rest states)
+        # their own oracle envelope (four runs from 1e-15-perturbed rest
+        # states; over 200 steps two runs miss some near-threshold stops)
+        seeds = (1, 2, 3, 4)
         pert = list(ex.map(_oracle_batch_case, [(oms[k], ms[k], nus[k], refs[k], nsteps, 1e-15, sd)
-                                                for k in loose for sd in (1, 2)]))
+                                                for k in loose for sd in seeds]))
+    ns = len(seeds)
     for j, k in enumerate(loose):
         its0, f0 = res[k]
-        its_p = [pert[2 * j][0], pert[2 * j + 1][0]]
+        runs = pert[ns * j:ns * (j + 1)]
+        its_p = [r[0] for r in runs]
         spread = {}
-        for its, f in (pert[2 * j], pert[2 * j + 1]):
+        for its, f in runs:
             for q, v in field_errors(f, f0).items():
                 spread[q] = max(spread.get(q, 0.0), v)
         assert_iters_where_well_conditioned(gpu_its[k], its0, its_p)
