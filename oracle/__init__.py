@@ -95,6 +95,10 @@ def lib(parallel: bool = False):
                                         C.c_double, C.c_int, C.c_int, C.c_double, _i32p, _f64p,
                                         dp]
             L.orc_piso_step.restype = C.c_int
+            L.orc_piso_step_sched.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_double,
+                                              C.c_int, C.c_int, C.c_double, _i32p, _i32p, _f64p,
+                                              dp]
+            L.orc_piso_step_sched.restype = C.c_int
             L.orc_simple_iter.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_double,
                                           C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
                                           C.c_int, C.c_double, _i32p, _f64p, dp, dp]
@@ -290,11 +294,19 @@ class Case:
         return self.get_fields(original_order=False)
 
     def piso_step(self, dt, n_corr=2, p_tol=1e-6, p_maxit=10000, u_tol=1e-10, u_maxit=1000,
-                  p_ref_cell=-1, p_ref=0.0, n_nonorth=0):
+                  p_ref_cell=-1, p_ref=0.0, n_nonorth=0, p_iters=None):
+        """One PISO step.  p_iters (optional): the iteration count of each
+        pressure solve, to replay another run's stopping decisions."""
         ns = 3 + n_corr * (n_nonorth + 1)
         its = np.zeros(ns, np.int32); res = np.zeros(2 * ns); ce = C.c_double()
-        st = self.L.orc_piso_step(self.h, dt, n_corr, n_nonorth, p_tol, p_maxit, u_tol, u_maxit,
-                                 p_ref_cell, p_ref, its, res, C.byref(ce))
+        if p_iters is not None:
+            sched = _c(p_iters, np.int32)
+            assert sched.size == ns - 3
+            st = self.L.orc_piso_step_sched(self.h, dt, n_corr, n_nonorth, u_tol, u_maxit,
+                                            p_ref_cell, p_ref, sched, its, res, C.byref(ce))
+        else:
+            st = self.L.orc_piso_step(self.h, dt, n_corr, n_nonorth, p_tol, p_maxit, u_tol,
+                                      u_maxit, p_ref_cell, p_ref, its, res, C.byref(ce))
         return dict(status=st, iters=its, res0=res[0::2], res=res[1::2], cont_err=ce.value)
 
     def simple_iter(self, alpha_u=0.7, alpha_p=0.3, p_tol=1e-10, p_reltol=0.01, p_maxit=10000,

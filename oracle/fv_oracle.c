@@ -1115,9 +1115,13 @@ int orc_case_set_pressure_solver(ocase *cs, int solver)
 /* Returns 0, or the first non-zero solver status.                            */
 /* ------------------------------------------------------------------------ */
 
-int orc_piso_step(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol, int p_maxit,
-                  double u_tol, int u_maxit, int ref_orig, double p_ref, int *iters, double *res,
-                  double *cont_err)
+/* p_sched (may be NULL): for replaying another implementation's run, the
+ * number of iterations each pressure solve takes, in the order of iters[3..]
+ * (the solve then runs exactly that many CG iterations: tolerance 0, limit
+ * p_sched[k]); the arithmetic of every iteration is unchanged. */
+static int piso_step_impl(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol,
+                          int p_maxit, double u_tol, int u_maxit, int ref_orig, double p_ref,
+                          int *iters, double *res, double *cont_err, const int *p_sched)
 {
     const omesh *m = cs->m;
     int N = m->N, F = m->F;
@@ -1147,8 +1151,12 @@ int orc_piso_step(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol,
             const int sk = 3 + k * (n_nonorth + 1) + j;
             if (j > 0) grad_p(cs, cs->p, gradp);
             assemble_pressure(cs, gradp, ref, p_ref, &w);
-            st = pressure_solve(cs, &w, p_tol, 0.0, p_maxit, &res[2 * sk], &res[2 * sk + 1],
-                                &iters[sk]);
+            if (p_sched)
+                st = pressure_solve(cs, &w, 0.0, 0.0, p_sched[sk - 3], &res[2 * sk],
+                                    &res[2 * sk + 1], &iters[sk]);
+            else
+                st = pressure_solve(cs, &w, p_tol, 0.0, p_maxit, &res[2 * sk], &res[2 * sk + 1],
+                                    &iters[sk]);
             if (st && !status) status = st;
         }
         correct_flux(cs, &w);
@@ -1159,6 +1167,25 @@ int orc_piso_step(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol,
     pwork_free(&w);
     free(gradp); free(gU); free(mdiag); free(up); free(lo); free(src); free(rhs);
     return status;
+}
+
+int orc_piso_step(ocase *cs, double dt, int n_corr, int n_nonorth, double p_tol, int p_maxit,
+                  double u_tol, int u_maxit, int ref_orig, double p_ref, int *iters, double *res,
+                  double *cont_err)
+{
+    return piso_step_impl(cs, dt, n_corr, n_nonorth, p_tol, p_maxit, u_tol, u_maxit, ref_orig,
+                          p_ref, iters, res, cont_err, NULL);
+}
+
+/* The PISO step with every pressure solve held to a given iteration count
+ * (p_sched [n_corr (1 + n_nonorth)]); a solve whose count is reached reports
+ * status -1 like any iteration-limited solve. */
+int orc_piso_step_sched(ocase *cs, double dt, int n_corr, int n_nonorth, double u_tol,
+                        int u_maxit, int ref_orig, double p_ref, const int *p_sched, int *iters,
+                        double *res, double *cont_err)
+{
+    return piso_step_impl(cs, dt, n_corr, n_nonorth, 0.0, 0, u_tol, u_maxit, ref_orig, p_ref,
+                          iters, res, cont_err, p_sched);
 }
 
 /* ------------------------------------------------------------------------ */

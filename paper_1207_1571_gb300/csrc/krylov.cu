@@ -486,6 +486,28 @@ __device__ __forceinline__ float spmv32_unit_row(const MixArgs &a, const RowSpan
     return acc;
 }
 
+// Rows i and i + 1 (i even) of the FP32 scaled matrix: they share a SELL
+// slice and sit in adjacent slots, so one 8-byte load brings both rows'
+// columns and both values of a slot.  The global form of k_pcg_mixed works
+// on row pairs this way: its passes stream from HBM, and with 4-byte loads
+// a thread keeps half the bytes in flight that the FP64 CG's 8-byte loads
+// do (8M cavity: 184 -> 163 us per inner iteration).  The resident form
+// keeps one row per thread (with pairs its L2- and latency-bound passes ran
+// slower: 18.0 -> 21.9 us per inner iteration on the 1M cavity).
+__device__ __forceinline__ float2 spmv32_unit_pair(const MixArgs &a, const RowSpan &rs, float2 pi)
+{
+    float2 acc = pi;
+#pragma unroll 6
+    for (int k = 0; k < rs.K; ++k) {
+        const int e = rs.e0 + 32 * k;
+        const int2 c = *reinterpret_cast<const int2 *>(a.col + e);
+        const float2 v = *reinterpret_cast<const float2 *>(a.val32 + e);
+        acc.x = fmaf(v.x, a.p[c.x], acc.x);
+        acc.y = fmaf(v.y, a.p[c.y], acc.y);
+    }
+    return acc;
+}
+
 // RES: the row-local FP32 vectors r^, q, e, w and v (each read and written
 // only by the thread that owns the row) live in the block's shared memory,
 // 5 x chunk floats of dynamic shared memory; p (gathered by neighbouring
@@ -503,6 +525,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
     const int rb = blockIdx.x * chunk;
     const int re = min(N, rb + chunk);
     const int i0 = rb + threadIdx.x;
+    const int ip = rb + 2 * (int)threadIdx.x;     // global form: first row of this thread's pairs
     extern __shared__ float resf[];
     // the FP32 row vectors, indexed by i - o: shared (offset by the block's
     // first row) or global
@@ -627,7 +650,7 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
             const float alpha = (float)sc.alpha, beta = (float)sc.beta, delta = (float)sc.delta;
             if (sc.restart) {
                 for (int i = i0; i < re; i += kCgBlock) a.p[i] = fmaf(-delta, wl[i - o], rl[i - o]);
-            } else {
+            } else if (RES) {
                 // all loads before the stores (as in the FP64 CG)
                 float *__restrict__ pv = a.p;
                 float *__restrict__ ev = el;
@@ -639,16 +662,59 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
                     ev[i - o] = fmaf(alpha, po, ei);
                     pv[i] = fmaf(-delta, wi, fmaf(beta, po, ri));
                 }
+            } else {
+                // global form: row pairs with 8-byte accesses, all loads before
+                // the stores; an odd last row alone
+                float *__restrict__ pv = a.p;
+                float *__restrict__ ev = el;
+                const float *__restrict__ rv = rl;
+                const float *__restrict__ wv = wl;
+#pragma unroll 2
+                for (int i = ip; i < re; i += 2 * kCgBlock) {
+                    if (i + 1 < re) {
+                        const float2 po = *reinterpret_cast<const float2 *>(pv + i);
+                        const float2 ei = *reinterpret_cast<const float2 *>(ev + i);
+                        const float2 ri = *reinterpret_cast<const float2 *>(rv + i);
+                        const float2 wi = *reinterpret_cast<const float2 *>(wv + i);
+                        *reinterpret_cast<float2 *>(ev + i) =
+                            make_float2(fmaf(alpha, po.x, ei.x), fmaf(alpha, po.y, ei.y));
+                        *reinterpret_cast<float2 *>(pv + i) =
+                            make_float2(fmaf(-delta, wi.x, fmaf(beta, po.x, ri.x)),
+                                        fmaf(-delta, wi.y, fmaf(beta, po.y, ri.y)));
+                    } else {
+                        const float po = pv[i], ei = ev[i], ri = rv[i], wi = wv[i];
+                        ev[i] = fmaf(alpha, po, ei);
+                        pv[i] = fmaf(-delta, wi, fmaf(beta, po, ri));
+                    }
+                }
             }
             if (!(ok = grid_sync(a.bar, gen, a.spin))) break;
             float pq32 = 0.0f;
+            if (RES) {
 #pragma unroll 2
-            for (int i = i0; i < re; i += kCgBlock) {
-                const RowSpan rs = row_span(a.slice_ptr, i);
-                const float pi = a.p[i];
-                const float acc = spmv32_unit_row(a, rs, pi);
-                ql[i - o] = acc;
-                pq32 = fmaf(pi, acc, pq32);
+                for (int i = i0; i < re; i += kCgBlock) {
+                    const RowSpan rs = row_span(a.slice_ptr, i);
+                    const float pi = a.p[i];
+                    const float acc = spmv32_unit_row(a, rs, pi);
+                    ql[i - o] = acc;
+                    pq32 = fmaf(pi, acc, pq32);
+                }
+            } else {
+                for (int i = ip; i < re; i += 2 * kCgBlock) {
+                    const RowSpan rs = row_span(a.slice_ptr, i);
+                    if (i + 1 < re) {
+                        const float2 pi = *reinterpret_cast<const float2 *>(a.p + i);
+                        const float2 acc = spmv32_unit_pair(a, rs, pi);
+                        *reinterpret_cast<float2 *>(ql + i) = acc;
+                        pq32 = fmaf(pi.x, acc.x, pq32);
+                        pq32 = fmaf(pi.y, acc.y, pq32);
+                    } else {
+                        const float pi = a.p[i];
+                        const float acc = spmv32_unit_row(a, rs, pi);
+                        ql[i] = acc;
+                        pq32 = fmaf(pi, acc, pq32);
+                    }
+                }
             }
             double v1[1] = {(double)pq32};
             if (!(ok = cg_grid_sum<1>(v1, a.partA, a.bar, gen, a.spin, buf, tot))) break;
@@ -666,13 +732,36 @@ __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
                 float *__restrict__ rv = rl;
                 const float *__restrict__ qv = ql;
                 const float *__restrict__ vv = vl;
+                if (RES) {
 #pragma unroll 4
-                for (int i = i0; i < re; i += kCgBlock) {
-                    const float qi = qv[i - o], rio = rv[i - o], vi = vv[i - o];
-                    const float ri = fmaf(-al, qi, rio);
-                    rv[i - o] = ri;
-                    rr32 = fmaf(ri, ri, rr32);
-                    vr32 = fmaf(vi, ri, vr32);
+                    for (int i = i0; i < re; i += kCgBlock) {
+                        const float qi = qv[i - o], rio = rv[i - o], vi = vv[i - o];
+                        const float ri = fmaf(-al, qi, rio);
+                        rv[i - o] = ri;
+                        rr32 = fmaf(ri, ri, rr32);
+                        vr32 = fmaf(vi, ri, vr32);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int i = ip; i < re; i += 2 * kCgBlock) {
+                        if (i + 1 < re) {
+                            const float2 qi = *reinterpret_cast<const float2 *>(qv + i);
+                            const float2 rio = *reinterpret_cast<const float2 *>(rv + i);
+                            const float2 vi = *reinterpret_cast<const float2 *>(vv + i);
+                            const float r0 = fmaf(-al, qi.x, rio.x), r1 = fmaf(-al, qi.y, rio.y);
+                            *reinterpret_cast<float2 *>(rv + i) = make_float2(r0, r1);
+                            rr32 = fmaf(r0, r0, rr32);
+                            rr32 = fmaf(r1, r1, rr32);
+                            vr32 = fmaf(vi.x, r0, vr32);
+                            vr32 = fmaf(vi.y, r1, vr32);
+                        } else {
+                            const float qi = qv[i], rio = rv[i], vi = vv[i];
+                            const float ri = fmaf(-al, qi, rio);
+                            rv[i] = ri;
+                            rr32 = fmaf(ri, ri, rr32);
+                            vr32 = fmaf(vi, ri, vr32);
+                        }
+                    }
                 }
             }
             double v2[2] = {(double)rr32, (double)vr32};

@@ -438,9 +438,13 @@ def test_cg_resident_and_global_forms_identical(P, monkeypatch, precision):
     """The CG keeps its row-local vectors (FP64: r^, q, y; mixed precision:
     the FP32 r^, q, e, w, v of the textbook order, p, s, e, w of the
     Chronopoulos-Gear order) in shared memory when a block's rows fit (meshes up to
-    about 1.2M cells on GB300) and in global memory otherwise; both
-    forms do the same arithmetic in the same order, so a mesh created with
-    FVGB_CG_RESIDENT=0 (global forms only) gives the same bits."""
+    about 1.2M cells on GB300) and in global memory otherwise.  The FP64 CG
+    and the Chronopoulos-Gear order do the same arithmetic in the same order
+    in both forms, so a mesh created with FVGB_CG_RESIDENT=0 (global forms
+    only) gives the same bits.  The textbook order's global form takes two
+    rows per thread in its inner passes (8-byte loads), which groups the FP32
+    per-thread sums differently: the same iteration counts and fields within
+    the solver tolerance's reach."""
     m = mg.permute_cells(mg.cavity3d(24), mg.random_permutation(24 ** 3, 5))
     prec = P.FV_PREC_FP64 if precision == "fp64" else P.FV_PREC_MIXED
     monkeypatch.setenv("FVGB_MIXED_CG", "classic" if precision == "mixed_classic" else "cgcg")
@@ -456,6 +460,13 @@ def test_cg_resident_and_global_forms_identical(P, monkeypatch, precision):
             its.append([int(k) for k in s["iters"]])
         out.append((case.get_fields_host(), its))
     (fa, ia), (fb, ib) = out
+    if precision == "mixed_classic":
+        assert np.abs(np.array(ia) - np.array(ib)).max() <= 2, (ia, ib)
+        for x, y, bar in zip(fa, fb, (1e-6, 1e-4, 1e-6)):
+            if bar == 1e-4:
+                x, y = x - x.mean(), y - y.mean()
+            assert rel(x, y) <= bar, rel(x, y)
+        return
     assert ia == ib
     for x, y in zip(fa, fb):
         assert np.array_equal(x, y)
