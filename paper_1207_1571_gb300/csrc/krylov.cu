@@ -1161,34 +1161,65 @@ struct BicgArgs {
     DevSolveStats *stats;
 };
 
-__device__ __forceinline__ double spmv_row(const BicgArgs &a, int i, double d, const double *vec)
+// A vec on row i for the components flagged in act: the row's coefficients
+// and columns are read once for all components; each component's sum runs
+// diagonal first, then the row's entries in slot order
+template <int NC>
+__device__ __forceinline__ void spmv_row_nc(const BicgArgs &a, int i, double d, const double *vec,
+                                            const bool (&act)[NC], double (&out)[NC])
 {
     const RowSpan rs = row_span(a.slice_ptr, i);
-    double acc = d * vec[i];
+    const size_t NN = (size_t)a.N;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = act[c] ? d * vec[c * NN + i] : 0.0;
     for (int k = 0; k < rs.K; ++k) {
         const int e = rs.e0 + 32 * k;
-        acc += a.val[e] * __ldcg(vec + a.col[e]);
+        const double v = a.val[e];
+        const size_t j = (size_t)a.col[e];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (act[c]) out[c] += v * __ldcg(vec + c * NN + j);
     }
-    return acc;
 }
 
+// Scalar state of a BiCGStab solve with NC right-hand sides, in shared memory
+// and updated by thread 0 after each grid sum (as CgScalars); each pass copies
+// the scalars it needs into registers.
+template <int NC>
+struct BicgScalars {
+    double rho[NC], rho_old[NC], alpha[NC], omega[NC], beta[NC];
+    double thr[NC], nb[NC], nr0[NC], nr[NC];
+    int active[NC], iters[NC], status[NC];
+    int n_active;
+};
+
+// NC components (1, or 3 for a momentum system) share the matrix.
+template <int NC>
 __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
 {
-    const int N = a.N, nc = a.ncomp;
+    constexpr int nc = NC;
+    const int N = a.N;
     const size_t NN = (size_t)N;
     const int stride = gridDim.x * kBlock;
     const int i0 = blockIdx.x * kBlock + threadIdx.x;
     unsigned gen = 0;
     bool ok = true;
+    __shared__ BicgScalars<NC> sc;
 
     // S: r = b - A x, rh = r, norms per component
     double v6[6] = {0, 0, 0, 0, 0, 0};   // ||b_c||^2, ||r_c||^2
+    bool act[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) act[c] = true;
     for (int i = i0; i < N; i += stride) {
         const double d = a.diag[i];
         a.dinv[i] = 1.0 / d;
+        double ax[NC];
+        spmv_row_nc<NC>(a, i, d, a.x, act, ax);
+#pragma unroll
         for (int c = 0; c < nc; ++c) {
             const double bi = a.b ? a.b[c * NN + i] : a.src[c * NN + i] - a.V[i] * a.gradp[c * NN + i];
-            const double ri = bi - spmv_row(a, i, d, a.x + c * NN);
+            const double ri = bi - ax[c];
             a.r[c * NN + i] = ri;
             a.rh[c * NN + i] = ri;
             v6[2 * c] += bi * bi;
@@ -1196,35 +1227,66 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
         }
     }
     ok = grid_sum<6>(v6, a.partB, a.bar, gen, a.spin);
-    double nb[3] = {0, 0, 0}, nr0[3] = {0, 0, 0}, nr[3] = {0, 0, 0}, thr[3] = {0, 0, 0};
-    double rho[3] = {1, 1, 1}, rho_old[3] = {1, 1, 1}, alpha[3] = {1, 1, 1}, omega[3] = {1, 1, 1};
-    int active[3] = {0, 0, 0}, zero[3] = {0, 0, 0}, iters[3] = {0, 0, 0}, status[3] = {0, 0, 0};
-    int n_active = 0;
-    if (ok) {
+    if (threadIdx.x == 0) {
+        sc.n_active = 0;
+#pragma unroll
         for (int c = 0; c < nc; ++c) {
-            nb[c] = sqrt(v6[2 * c]);
-            nr0[c] = nr[c] = sqrt(v6[2 * c + 1]);
-            thr[c] = fmax(a.tol * nb[c], a.reltol * nr0[c]);
-            rho[c] = v6[2 * c + 1];
-            if (nb[c] == 0.0) { zero[c] = 1; nr0[c] = nr[c] = 0.0; }
-            else if (nr0[c] > thr[c]) { active[c] = 1; ++n_active; }
+            sc.rho[c] = sc.rho_old[c] = sc.alpha[c] = sc.omega[c] = sc.beta[c] = 1.0;
+            sc.thr[c] = sc.nb[c] = sc.nr0[c] = sc.nr[c] = 0.0;
+            sc.active[c] = sc.iters[c] = sc.status[c] = 0;
+            if (!ok) continue;
+            const double nb = sqrt(v6[2 * c]);
+            const double nr0 = sqrt(v6[2 * c + 1]);
+            sc.thr[c] = fmax(a.tol * nb, a.reltol * nr0);
+            sc.rho[c] = v6[2 * c + 1];
+            sc.nb[c] = nb;
+            if (nb != 0.0) {
+                sc.nr0[c] = sc.nr[c] = nr0;
+                if (nr0 > sc.thr[c]) { sc.active[c] = 1; ++sc.n_active; }
+            }
         }
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
         for (int c = 0; c < nc; ++c)
-            if (zero[c])
+            if (sc.nb[c] == 0.0)
                 for (int i = i0; i < N; i += stride) a.x[c * NN + i] = 0.0;
     }
     int it = 0;
-    while (ok && n_active > 0) {
+    while (ok && sc.n_active > 0) {
         ++it;
         // P1: p = r + beta (p - omega v); y = D^-1 p
-        double beta[3];
-        for (int c = 0; c < nc; ++c) beta[c] = (rho[c] / rho_old[c]) * (alpha[c] / omega[c]);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < nc; ++c)
+                sc.beta[c] = (sc.rho[c] / sc.rho_old[c]) * (sc.alpha[c] / sc.omega[c]);
+        }
+        __syncthreads();
+        double beta[NC], omega[NC];
+#pragma unroll
+        for (int c = 0; c < nc; ++c) {
+            act[c] = sc.active[c] != 0;
+            beta[c] = sc.beta[c];
+            omega[c] = sc.omega[c];
+        }
         for (int i = i0; i < N; i += stride) {
+            // every component's loads are issued before the first store
             const double di = a.dinv[i];
+            double rr[NC], pp[NC], vv[NC];
+#pragma unroll
             for (int c = 0; c < nc; ++c) {
-                if (!active[c]) continue;
+                rr[c] = pp[c] = vv[c] = 0.0;
+                if (!act[c]) continue;
                 const size_t j = c * NN + i;
-                const double pn = (it == 1) ? a.r[j] : a.r[j] + beta[c] * (a.p[j] - omega[c] * a.v[j]);
+                rr[c] = a.r[j];
+                if (it > 1) { pp[c] = a.p[j]; vv[c] = a.v[j]; }
+            }
+#pragma unroll
+            for (int c = 0; c < nc; ++c) {
+                if (!act[c]) continue;
+                const size_t j = c * NN + i;
+                const double pn = (it == 1) ? rr[c] : rr[c] + beta[c] * (pp[c] - omega[c] * vv[c]);
                 a.p[j] = pn;
                 a.y[j] = pn * di;
             }
@@ -1234,30 +1296,50 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
         double v3[3] = {0, 0, 0};
         for (int i = i0; i < N; i += stride) {
             const double d = a.diag[i];
+            double rh[NC], ay[NC];
+#pragma unroll
+            for (int c = 0; c < nc; ++c) rh[c] = act[c] ? a.rh[c * NN + i] : 0.0;
+            spmv_row_nc<NC>(a, i, d, a.y, act, ay);
+#pragma unroll
             for (int c = 0; c < nc; ++c) {
-                if (!active[c]) continue;
-                const size_t j = c * NN + i;
-                const double vi = spmv_row(a, i, d, a.y + c * NN);
-                a.v[j] = vi;
-                v3[c] += a.rh[j] * vi;
+                if (!act[c]) continue;
+                a.v[c * NN + i] = ay[c];
+                v3[c] += rh[c] * ay[c];
             }
         }
         if (!(ok = grid_sum<3>(v3, a.partA, a.bar, gen, a.spin))) break;
-        for (int c = 0; c < nc; ++c) {
-            if (!active[c]) continue;
-            if (v3[c] == 0.0 || !isfinite(v3[c])) {
-                status[c] = FV_E_DIVERGED; iters[c] = it; active[c] = 0; --n_active;
-            } else {
-                alpha[c] = rho[c] / v3[c];
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < nc; ++c) {
+                if (!sc.active[c]) continue;
+                if (v3[c] == 0.0 || !isfinite(v3[c])) {
+                    sc.status[c] = FV_E_DIVERGED; sc.iters[c] = it; sc.active[c] = 0; --sc.n_active;
+                } else {
+                    sc.alpha[c] = sc.rho[c] / v3[c];
+                }
             }
+        }
+        __syncthreads();
+        double alpha[NC];
+#pragma unroll
+        for (int c = 0; c < nc; ++c) {
+            act[c] = sc.active[c] != 0;
+            alpha[c] = sc.alpha[c];
         }
         // P3: s = r - alpha v; z = D^-1 s
         for (int i = i0; i < N; i += stride) {
             const double di = a.dinv[i];
+            double rr[NC], vv[NC];
+#pragma unroll
             for (int c = 0; c < nc; ++c) {
-                if (!active[c]) continue;
+                rr[c] = act[c] ? a.r[c * NN + i] : 0.0;
+                vv[c] = act[c] ? a.v[c * NN + i] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < nc; ++c) {
+                if (!act[c]) continue;
                 const size_t j = c * NN + i;
-                const double si = a.r[j] - alpha[c] * a.v[j];
+                const double si = rr[c] - alpha[c] * vv[c];
                 a.s[j] = si;
                 a.z[j] = si * di;
             }
@@ -1267,51 +1349,78 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BicgArgs a)
         double w6[6] = {0, 0, 0, 0, 0, 0};
         for (int i = i0; i < N; i += stride) {
             const double d = a.diag[i];
+            double ss[NC], az[NC];
+#pragma unroll
+            for (int c = 0; c < nc; ++c) ss[c] = act[c] ? a.s[c * NN + i] : 0.0;
+            spmv_row_nc<NC>(a, i, d, a.z, act, az);
+#pragma unroll
             for (int c = 0; c < nc; ++c) {
-                if (!active[c]) continue;
-                const size_t j = c * NN + i;
-                const double ti = spmv_row(a, i, d, a.z + c * NN);
-                a.t[j] = ti;
-                w6[2 * c] += ti * a.s[j];
+                if (!act[c]) continue;
+                const double ti = az[c];
+                a.t[c * NN + i] = ti;
+                w6[2 * c] += ti * ss[c];
                 w6[2 * c + 1] += ti * ti;
             }
         }
         if (!(ok = grid_sum<6>(w6, a.partB, a.bar, gen, a.spin))) break;
-        for (int c = 0; c < nc; ++c)
-            if (active[c]) omega[c] = w6[2 * c + 1] > 0.0 ? w6[2 * c] / w6[2 * c + 1] : 0.0;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < nc; ++c)
+                if (sc.active[c]) sc.omega[c] = w6[2 * c + 1] > 0.0 ? w6[2 * c] / w6[2 * c + 1] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < nc; ++c) omega[c] = sc.omega[c];
         // P5: x += alpha y + omega z; r = s - omega t; rh.r, r.r
         double u6[6] = {0, 0, 0, 0, 0, 0};
         for (int i = i0; i < N; i += stride) {
+            double xn[NC], rn[NC], rh[NC];
+#pragma unroll
             for (int c = 0; c < nc; ++c) {
-                if (!active[c]) continue;
+                xn[c] = rn[c] = rh[c] = 0.0;
+                if (!act[c]) continue;
                 const size_t j = c * NN + i;
-                a.x[j] += alpha[c] * a.y[j] + omega[c] * a.z[j];
-                const double ri = a.s[j] - omega[c] * a.t[j];
-                a.r[j] = ri;
-                u6[2 * c] += a.rh[j] * ri;
-                u6[2 * c + 1] += ri * ri;
+                xn[c] = a.x[j] + (alpha[c] * a.y[j] + omega[c] * a.z[j]);
+                rn[c] = a.s[j] - omega[c] * a.t[j];
+                rh[c] = a.rh[j];
+            }
+#pragma unroll
+            for (int c = 0; c < nc; ++c) {
+                if (!act[c]) continue;
+                const size_t j = c * NN + i;
+                a.x[j] = xn[c];
+                a.r[j] = rn[c];
+                u6[2 * c] += rh[c] * rn[c];
+                u6[2 * c + 1] += rn[c] * rn[c];
             }
         }
         if (!(ok = grid_sum<6>(u6, a.partA, a.bar, gen, a.spin))) break;
-        for (int c = 0; c < nc; ++c) {
-            if (!active[c]) continue;
-            nr[c] = sqrt(u6[2 * c + 1]);
-            int stop = 0;
-            if (!isfinite(nr[c])) { status[c] = FV_E_DIVERGED; stop = 1; }
-            else if (nr[c] <= thr[c]) { stop = 1; }
-            else if (it >= a.maxit) { status[c] = FV_E_NOT_CONVERGED; stop = 1; }
-            else if (omega[c] == 0.0) { status[c] = FV_E_DIVERGED; stop = 1; }
-            if (stop) { iters[c] = it; active[c] = 0; --n_active; }
-            rho_old[c] = rho[c];
-            rho[c] = u6[2 * c];
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < nc; ++c) {
+                if (!sc.active[c]) continue;
+                const double nr = sqrt(u6[2 * c + 1]);
+                sc.nr[c] = nr;
+                int stop = 0;
+                if (!isfinite(nr)) { sc.status[c] = FV_E_DIVERGED; stop = 1; }
+                else if (nr <= sc.thr[c]) { stop = 1; }
+                else if (it >= a.maxit) { sc.status[c] = FV_E_NOT_CONVERGED; stop = 1; }
+                else if (sc.omega[c] == 0.0) { sc.status[c] = FV_E_DIVERGED; stop = 1; }
+                if (stop) { sc.iters[c] = it; sc.active[c] = 0; --sc.n_active; }
+                sc.rho_old[c] = sc.rho[c];
+                sc.rho[c] = u6[2 * c];
+            }
         }
+        __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
         for (int c = 0; c < nc; ++c) {
-            a.stats[c].iters = iters[c];
-            a.stats[c].status = ok ? status[c] : FV_E_TIMEOUT;
-            a.stats[c].res0 = nb[c] > 0.0 ? nr0[c] / nb[c] : 0.0;
-            a.stats[c].res = nb[c] > 0.0 ? nr[c] / nb[c] : 0.0;
+            const double nb = sc.nb[c];
+            a.stats[c].iters = sc.iters[c];
+            a.stats[c].status = ok ? sc.status[c] : FV_E_TIMEOUT;
+            a.stats[c].res0 = nb > 0.0 ? sc.nr0[c] / nb : 0.0;
+            a.stats[c].res = nb > 0.0 ? sc.nr[c] / nb : 0.0;
             a.stats[c].outer = 1;
         }
     }
@@ -1412,7 +1521,7 @@ fv_status krylov_setup(fv_mesh *m)
     FV_CHECK(per_sm >= 1, FV_E_CUDA, "mixed CG kernel cannot be resident");
     w.Gcg = m->sm_count;
     int per_sm2 = 0;
-    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_bicgstab, kBlock, 0));
+    FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_bicgstab<3>, kBlock, 0));
     FV_CHECK(per_sm2 >= 1, FV_E_CUDA, "BiCGStab kernel cannot be resident");
     w.block = kBlock;
     w.G = m->sm_count * (per_sm2 < 2 ? per_sm2 : 2);
@@ -1622,8 +1731,10 @@ fv_status launch_bicgstab(const fv_mesh *m, const BicgProblem &pb)
     a.stats = pb.stats;
     FV_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), m->stream));
     void *args[] = {&a};
-    return coop_launch((const void *)k_bicgstab, grid_for(m->N, kBlock, w.G), kBlock, args,
-                       m->stream);
+    FV_CHECK(pb.ncomp == 1 || pb.ncomp == 3, FV_E_INVALID, "BiCGStab takes 1 or 3 components, got %d",
+             pb.ncomp);
+    const void *fn = pb.ncomp == 3 ? (const void *)k_bicgstab<3> : (const void *)k_bicgstab<1>;
+    return coop_launch(fn, grid_for(m->N, kBlock, w.G), kBlock, args, m->stream);
 }
 
 }  // namespace fvgb
