@@ -54,6 +54,15 @@ static MeshView view(const fv_mesh *m)
 
 static int blocks_for(int n) { return (n + kAsmBlock - 1) / kAsmBlock; }
 
+// x with its sign flipped when neg (the face value as seen from the
+// neighbour cell).  Integer operations on the sign bit: a multiply by -1
+// would take the FP64 pipe, which bounds these kernels.  Bit-identical to
+// (neg ? -1.0 : 1.0) * x, so every sum keeps its rounding.
+__device__ __forceinline__ double with_sign(double x, bool neg)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+}
+
 // ------------------------------------------------------------ momentum --
 
 struct MomArgs {
@@ -88,16 +97,15 @@ __global__ void __launch_bounds__(kAsmBlock) k_momentum(MeshView m, MomArgs a)
         const double w = m.w[f];
         const double wS = own ? w : 1.0 - w;       // weight of this cell on the face
         const double wO = own ? 1.0 - w : w;       // weight of the other cell
-        const double sg = own ? 1.0 : -1.0;
-        const double Fo = sg * a.phi[f];           // flux out of this cell
+        const double Fo = with_sign(a.phi[f], !own);   // flux out of this cell
         const double D = nu * m.magSf[f] * m.delta[f];
         diag += Fo * wS;
         diag += D;
         a.Mo[e] = Fo * wO - D;
-        const double pf = w * a.p[lo] + (1.0 - w) * a.p[hi];
-        g0 += sg * m.Sf[f] * pf;
-        g1 += sg * m.Sf[m.M + f] * pf;
-        g2 += sg * m.Sf[2 * m.M + f] * pf;
+        const double pf = with_sign(w * a.p[lo] + (1.0 - w) * a.p[hi], !own);
+        g0 += m.Sf[f] * pf;
+        g1 += m.Sf[m.M + f] * pf;
+        g2 += m.Sf[2 * m.M + f] * pf;
         if (m.nonorth) {
             const double k0 = m.kv[f], k1 = m.kv[m.F + f], k2 = m.kv[2 * m.F + f];
             double t[3];
@@ -108,9 +116,9 @@ __global__ void __launch_bounds__(kAsmBlock) k_momentum(MeshView m, MomArgs a)
                 const double gz = w * G[2 * N + lo] + (1.0 - w) * G[2 * N + hi];
                 t[cc] = nu * m.magSf[f] * (k0 * gx + k1 * gy + k2 * gz);
             }
-            src0 += sg * t[0];
-            src1 += sg * t[1];
-            src2 += sg * t[2];
+            src0 += with_sign(t[0], !own);
+            src1 += with_sign(t[1], !own);
+            src2 += with_sign(t[2], !own);
         }
     }
     for (int j = m.bptr[i]; j < m.bptr[i + 1]; ++j) {
@@ -170,8 +178,9 @@ __global__ void __launch_bounds__(kAsmBlock) k_grad_u(MeshView m, const double *
         const int c = m.col[e];
         const bool own = i < c;
         const int lo = own ? i : c, hi = own ? c : i;
-        const double w = m.w[f], sg = own ? 1.0 : -1.0;
-        const double S0 = sg * m.Sf[f], S1 = sg * m.Sf[m.M + f], S2 = sg * m.Sf[2 * m.M + f];
+        const double w = m.w[f];
+        const double S0 = with_sign(m.Sf[f], !own), S1 = with_sign(m.Sf[m.M + f], !own),
+                     S2 = with_sign(m.Sf[2 * m.M + f], !own);
         for (int cc = 0; cc < 3; ++cc) {
             const double uf = w * u[cc * N + lo] + (1.0 - w) * u[cc * N + hi];
             g[3 * cc] += S0 * uf;
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(kAsmBlock) k_pressure(MeshView m, PresArgs a)
         const int c = m.col[e];
         const bool own = i < c;
         const int lo = own ? i : c, hi = own ? c : i;
-        const double w = m.w[f], sg = own ? 1.0 : -1.0;
+        const double w = m.w[f];
         const double S0 = m.Sf[f], S1 = m.Sf[m.M + f], S2 = m.Sf[2 * m.M + f];
         const double h0 = w * a.HbyA[lo] + (1.0 - w) * a.HbyA[hi];
         const double h1 = w * a.HbyA[N + lo] + (1.0 - w) * a.HbyA[N + hi];
@@ -259,14 +268,14 @@ __global__ void __launch_bounds__(kAsmBlock) k_pressure(MeshView m, PresArgs a)
         const double af = rf * m.magSf[f] * m.delta[f];
         diag += af;
         a.Po[e] = -af;
-        bb -= sg * ph;
+        bb -= with_sign(ph, !own);
         double nf = 0.0;
         if (m.nonorth) {
             const double gx = w * a.gradp[lo] + (1.0 - w) * a.gradp[hi];
             const double gy = w * a.gradp[N + lo] + (1.0 - w) * a.gradp[N + hi];
             const double gz = w * a.gradp[2 * N + lo] + (1.0 - w) * a.gradp[2 * N + hi];
             nf = rf * m.magSf[f] * (m.kv[f] * gx + m.kv[m.F + f] * gy + m.kv[2 * m.F + f] * gz);
-            bb += sg * nf;
+            bb += with_sign(nf, !own);
         }
         if (own) {
             a.phis[f] = ph;
@@ -328,11 +337,12 @@ __global__ void __launch_bounds__(kAsmBlock) k_correct(MeshView m, CorrArgs a)
         const int c = m.col[e];
         const bool own = i < c;
         const int lo = own ? i : c, hi = own ? c : i;
-        const double w = m.w[f], sg = own ? 1.0 : -1.0;
-        const double pf = w * a.p[lo] + (1.0 - w) * a.p[hi];
-        g0 += sg * m.Sf[f] * pf;
-        g1 += sg * m.Sf[m.M + f] * pf;
-        g2 += sg * m.Sf[2 * m.M + f] * pf;
+        const double w = m.w[f];
+        // face value as seen from this cell
+        const double pf = with_sign(w * a.p[lo] + (1.0 - w) * a.p[hi], !own);
+        g0 += m.Sf[f] * pf;
+        g1 += m.Sf[m.M + f] * pf;
+        g2 += m.Sf[2 * m.M + f] * pf;
         if (own) {
             double v = a.phis[f] - a.af[f] * (a.p[c] - pP);
             if (m.nonorth) v -= a.nof[f];
@@ -385,11 +395,12 @@ __global__ void __launch_bounds__(kAsmBlock) k_grad_p(MeshView m, const double *
         const int c = m.col[e];
         const bool own = i < c;
         const int lo = own ? i : c, hi = own ? c : i;
-        const double w = m.w[f], sg = own ? 1.0 : -1.0;
-        const double pf = w * p[lo] + (1.0 - w) * p[hi];
-        g0 += sg * m.Sf[f] * pf;
-        g1 += sg * m.Sf[m.M + f] * pf;
-        g2 += sg * m.Sf[2 * m.M + f] * pf;
+        const double w = m.w[f];
+        // face value as seen from this cell
+        const double pf = with_sign(w * p[lo] + (1.0 - w) * p[hi], !own);
+        g0 += m.Sf[f] * pf;
+        g1 += m.Sf[m.M + f] * pf;
+        g2 += m.Sf[2 * m.M + f] * pf;
     }
     for (int j = m.bptr[i]; j < m.bptr[i + 1]; ++j) {
         const int b = m.bface[j];
@@ -451,11 +462,12 @@ __global__ void __launch_bounds__(kAsmBlock) k_grad_correct_u(MeshView m, CorrAr
         const int c = m.col[e];
         const bool own = i < c;
         const int lo = own ? i : c, hi = own ? c : i;
-        const double w = m.w[f], sg = own ? 1.0 : -1.0;
-        const double pf = w * pg[lo] + (1.0 - w) * pg[hi];
-        g0 += sg * m.Sf[f] * pf;
-        g1 += sg * m.Sf[m.M + f] * pf;
-        g2 += sg * m.Sf[2 * m.M + f] * pf;
+        const double w = m.w[f];
+        // face value as seen from this cell
+        const double pf = with_sign(w * pg[lo] + (1.0 - w) * pg[hi], !own);
+        g0 += m.Sf[f] * pf;
+        g1 += m.Sf[m.M + f] * pf;
+        g2 += m.Sf[2 * m.M + f] * pf;
     }
     for (int j = m.bptr[i]; j < m.bptr[i + 1]; ++j) {
         const int b = m.bface[j];
@@ -606,11 +618,12 @@ __global__ void k_gauss_grad(MeshView m, const double *__restrict__ x, const dou
         const int c = m.col[e];
         const bool own = i < c;
         const int lo = own ? i : c, hi = own ? c : i;
-        const double w = m.w[f], sg = own ? 1.0 : -1.0;
-        const double xf = w * x[lo] + (1.0 - w) * x[hi];
-        g0 += sg * m.Sf[f] * xf;
-        g1 += sg * m.Sf[m.M + f] * xf;
-        g2 += sg * m.Sf[2 * m.M + f] * xf;
+        const double w = m.w[f];
+        // face value as seen from this cell
+        const double xf = with_sign(w * x[lo] + (1.0 - w) * x[hi], !own);
+        g0 += m.Sf[f] * xf;
+        g1 += m.Sf[m.M + f] * xf;
+        g2 += m.Sf[2 * m.M + f] * xf;
     }
     for (int j = m.bptr[i]; j < m.bptr[i + 1]; ++j) {
         const int b = m.bface[j];

@@ -642,15 +642,24 @@ struct BBi {
     DevSolveStats *stats;
 };
 
-__device__ __forceinline__ double bspmv(const BBi &a, int i, double d, const double *vec)
+// A vec on row i for the components flagged in act, the row's coefficients
+// read once for all three; each component's sum runs diagonal first, then
+// the row's entries in slot order
+__device__ __forceinline__ void bspmv3(const BBi &a, int i, double d, const double *vec,
+                                       const int (&act)[3], double (&out)[3])
 {
     const RowS rs = rowspan(a.slice_ptr, i);
-    double acc = d * vec[i];
+    const size_t NN = a.N;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = act[c] ? d * vec[c * NN + i] : 0.0;
     for (int k = 0; k < rs.K; ++k) {
         const int e = rs.e0 + 32 * k;
-        acc += a.val[e] * vec[a.col[e]];
+        const double v = a.val[e];
+        const size_t j = (size_t)a.col[e];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (act[c]) out[c] += v * vec[c * NN + j];
     }
-    return acc;
 }
 
 template <int BLOCK, int U, int RED>
@@ -669,12 +678,15 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
         const int r0 = a.start[cid], r1 = r0 + a.count[cid];
         const int i0 = r0 + threadIdx.x;
         double v6[6] = {0, 0, 0, 0, 0, 0};
+        const int all[3] = {1, 1, 1};
         for (int i = i0; i < r1; i += BLOCK) {
             const double d = a.diag[i];
             a.dinv[i] = 1.0 / d;
+            double ax[3];
+            bspmv3(a, i, d, a.x, all, ax);
             for (int c = 0; c < 3; ++c) {
                 const double bi = a.src[c * NN + i] - a.V[i] * a.gradp[c * NN + i];
-                const double ri = bi - bspmv(a, i, d, a.x + c * NN);
+                const double ri = bi - ax[c];
                 a.r[c * NN + i] = ri;
                 a.rh[c * NN + i] = ri;
                 v6[2 * c] += bi * bi;
@@ -714,11 +726,22 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
             }
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
+                // every component's loads are issued before the first store
                 const double di = a.dinv[i];
+                double rr[3], pp[3], vv[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    rr[c] = pp[c] = vv[c] = 0.0;
+                    if (!act[c]) continue;
+                    const size_t j = c * NN + i;
+                    rr[c] = a.r[j];
+                    if (it > 1) { pp[c] = a.p[j]; vv[c] = a.v[j]; }
+                }
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (!act[c]) continue;
                     const size_t j = c * NN + i;
-                    const double pn = it == 1 ? a.r[j] : a.r[j] + beta[c] * (a.p[j] - omega[c] * a.v[j]);
+                    const double pn = it == 1 ? rr[c] : rr[c] + beta[c] * (pp[c] - omega[c] * vv[c]);
                     a.p[j] = pn;
                     a.y[j] = pn * di;
                 }
@@ -728,12 +751,15 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
                 const double d = a.diag[i];
+                double rh[3], ay[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) rh[c] = act[c] ? a.rh[c * NN + i] : 0.0;
+                bspmv3(a, i, d, a.y, act, ay);
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (!act[c]) continue;
-                    const size_t j = c * NN + i;
-                    const double vi = bspmv(a, i, d, a.y + c * NN);
-                    a.v[j] = vi;
-                    v3[c] += a.rh[j] * vi;
+                    a.v[c * NN + i] = ay[c];
+                    v3[c] += rh[c] * ay[c];
                 }
             }
             bsum<BLOCK, RED, 3>(v3, tot);
@@ -752,10 +778,17 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
                 const double di = a.dinv[i];
+                double rr[3], vv[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    rr[c] = act[c] ? a.r[c * NN + i] : 0.0;
+                    vv[c] = act[c] ? a.v[c * NN + i] : 0.0;
+                }
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (!act[c]) continue;
                     const size_t j = c * NN + i;
-                    const double si = a.r[j] - alpha[c] * a.v[j];
+                    const double si = rr[c] - alpha[c] * vv[c];
                     a.s[j] = si;
                     a.z[j] = si * di;
                 }
@@ -765,12 +798,16 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
                 const double d = a.diag[i];
+                double ss[3], az[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ss[c] = act[c] ? a.s[c * NN + i] : 0.0;
+                bspmv3(a, i, d, a.z, act, az);
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (!act[c]) continue;
-                    const size_t j = c * NN + i;
-                    const double ti = bspmv(a, i, d, a.z + c * NN);
-                    a.t[j] = ti;
-                    w6[2 * c] += ti * a.s[j];
+                    const double ti = az[c];
+                    a.t[c * NN + i] = ti;
+                    w6[2 * c] += ti * ss[c];
                     w6[2 * c + 1] += ti * ti;
                 }
             }
@@ -783,14 +820,24 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
             double u6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
+                double xn[3], rn[3], rh[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xn[c] = rn[c] = rh[c] = 0.0;
+                    if (!act[c]) continue;
+                    const size_t j = c * NN + i;
+                    xn[c] = a.x[j] + (alpha[c] * a.y[j] + omega[c] * a.z[j]);
+                    rn[c] = a.s[j] - omega[c] * a.t[j];
+                    rh[c] = a.rh[j];
+                }
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (!act[c]) continue;
                     const size_t j = c * NN + i;
-                    a.x[j] += alpha[c] * a.y[j] + omega[c] * a.z[j];
-                    const double ri = a.s[j] - omega[c] * a.t[j];
-                    a.r[j] = ri;
-                    u6[2 * c] += a.rh[j] * ri;
-                    u6[2 * c + 1] += ri * ri;
+                    a.x[j] = xn[c];
+                    a.r[j] = rn[c];
+                    u6[2 * c] += rh[c] * rn[c];
+                    u6[2 * c + 1] += rn[c] * rn[c];
                 }
             }
             bsum<BLOCK, RED, 6>(u6, tot);
