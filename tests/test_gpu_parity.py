@@ -154,10 +154,12 @@ def test_pcg_degenerate_cases(P):
     assert rel(x.cpu().numpy(), xo) <= TOL
 
 
-@pytest.mark.parametrize("which", ["2d", "tet"])
+@pytest.mark.parametrize("which", ["2d", "tet", "3d_big"])
 def test_bicgstab_matches_oracle(P, which):
     if which == "2d":
         m, nu, dt = mg.cavity2d(16), 0.02, 0.05
+    elif which == "3d_big":
+        m, nu, dt = mg.cavity3d(24), 0.01, 0.01          # several blocks, grid sums
     else:
         m, nu, dt = mg.tet_box(3, 3, 3, jitter=0.1), 0.02, 0.05
         m.patches[0].u = (1.0, 0.0, 0.5)
@@ -175,6 +177,37 @@ def test_bicgstab_matches_oracle(P, which):
         s = mesh.bicgstab_solve(t64(d), t64(up), t64(lo), t64(src[0]), x, tol=tol)
         assert s["status"] == 0 and abs(s["iters"] - ito) <= 1, (s, ito)
         assert rel(x.cpu().numpy(), xo) <= TOL
+
+
+def test_bicgstab_degenerate_cases(P):
+    """Zero right-hand side, an exact start and the iteration limit, on a
+    momentum system large enough for several blocks (grid sums)."""
+    m = mg.cavity3d(12)
+    om = O.Mesh(m, renumber=True)
+    oc = O.Case(om, 0.01)
+    oc.piso_step(0.01, 2, p_ref_cell=m.corner_cell)
+    d, up, lo, src = oc.momentum_system(True, 0.01)
+    own, nei = om.addressing()
+    mesh = P.Mesh(m, renumber=True)
+    b = src[0]
+    # zero right-hand side: x = 0 without iterating
+    x = t64(np.ones(m.n_cells))
+    s = mesh.bicgstab_solve(t64(d), t64(up), t64(lo), t64(0 * b), x)
+    assert s["iters"] == 0 and s["status"] == 0 and not x.cpu().numpy().any()
+    # exact start: no iteration
+    xs = O.bicgstab(own, nei, d, up, lo, b, np.zeros(m.n_cells), tol=1e-15, maxit=200)[0]
+    x = t64(xs)
+    s = mesh.bicgstab_solve(t64(d), t64(up), t64(lo), t64(b), x, tol=1e-8)
+    assert s["iters"] == 0 and s["status"] == 0
+    # iteration limit: NOT_CONVERGED after exactly maxit iterations, the
+    # oracle's iterate and residual
+    x = t64(np.zeros(m.n_cells))
+    s = mesh.bicgstab_solve(t64(d), t64(up), t64(lo), t64(b), x, tol=1e-15, maxit=3)
+    xo, ito, r0o, r1o, sto = O.bicgstab(own, nei, d, up, lo, b, np.zeros(m.n_cells), tol=1e-15,
+                                        maxit=3)
+    assert s["status"] == 4 and sto == -1 and s["iters"] == ito == 3
+    assert rel(x.cpu().numpy(), xo) <= TOL
+    assert abs(s["res"] - r1o) <= 1e-9 * r1o and abs(s["res0"] - r0o) <= 1e-12 * r0o
 
 
 # -------------------------------------------------------------- PISO step --
