@@ -511,8 +511,10 @@ __device__ __forceinline__ float2 spmv32_unit_pair(const MixArgs &a, const RowSp
 // RES: the row-local FP32 vectors r^, q, e, w and v (each read and written
 // only by the thread that owns the row) live in the block's shared memory,
 // 5 x chunk floats of dynamic shared memory; p (gathered by neighbouring
-// rows), the matrices and the FP64 vectors stay in global memory.  Both forms
-// do the same arithmetic in the same order.
+// rows), the matrices and the FP64 vectors stay in global memory.  The global
+// form takes two neighbouring rows per thread in its inner passes (8-byte
+// accesses), which groups the per-thread sums differently from the resident
+// form.
 template <bool RES>
 __global__ void __launch_bounds__(kCgBlock, 1) k_pcg_mixed(MixArgs a)
 {
