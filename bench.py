@@ -850,7 +850,8 @@ def run_batch(args, ws, rank, precision=None, line=True, loop=True):
     gbs = bytes_cg / (pm[4] / 1e3) / 1e9 if pm[4] > 0 else None
     roof = {"bound": "hbm", "kernel": kern, "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": gbs / peak if gbs else None, "peak_kind": peak_kind, "algorithmic": alg,
-            "cg_share_of_direct_steps": pm[4] / sum(pm[k] for k in range(7)) if pm[4] else None}
+            "cg_share_of_direct_steps": pm[4] / sum(pm[k] for k in range(7)) if pm[4] else None,
+            "direct_steps_stage_ms": {n: pm[k] / 2 for k, n in enumerate(_capi.PROF_STAGES)}}
     value = ws * ncell * args.steps / t
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,

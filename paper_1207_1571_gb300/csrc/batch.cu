@@ -50,9 +50,9 @@ constexpr int kStatStride = 3 + FV_MAX_CORR;
 
 // block = threads per block, unroll = rows per thread per loop trip,
 // red = block reduction (0 shuffle tree, 1 shared-memory staging),
-// cl = blocks per case for the pressure solve (a thread-block cluster
-// sharing one case through distributed shared memory; the momentum solve
-// always uses one block of at most 512 threads per case).
+// cl = blocks per case for the pressure and momentum solves (a thread-block
+// cluster sharing one case through distributed shared memory; the momentum
+// solve uses blocks of at most 512 threads).
 struct Sched {
     int block, unroll, red, cl;
 };
@@ -158,7 +158,7 @@ __device__ __forceinline__ int next_case(int32_t *counter, int *slot)
 }
 
 // ---------------------------------------------------- cluster helpers ----
-// A case of the pressure solve is owned by a cluster of CL blocks (CL = 1:
+// A case of a solve is owned by a cluster of CL blocks (CL = 1:
 // one block).  Phases are separated by a cluster barrier (release/acquire at
 // cluster scope, so rows written by one block are visible to the others);
 // reductions add the CL block totals, read through distributed shared
@@ -662,20 +662,26 @@ __device__ __forceinline__ void bspmv3(const BBi &a, int i, double d, const doub
     }
 }
 
-template <int BLOCK, int U, int RED>
+// A case is owned by a cluster of CL blocks (rows split evenly between them),
+// with the cluster barriers and sums of the pressure solve; CL = 1: one block.
+template <int BLOCK, int U, int RED, int CL>
 __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
 {
     __shared__ int slot;
-    __shared__ double tot[6];
+    __shared__ double tot[6], cpart[16];
     __shared__ double s_nb[3], s_nr0[3], s_nr[3], s_thr[3], s_rho[3], s_rho_old[3], s_alpha[3],
         s_omega[3];
     __shared__ int s_active[3], s_iters[3], s_status[3], s_zero[3], s_nact;
     const size_t NN = a.N;
+    const int rank = CL == 1 ? 0 : (int)cooperative_groups::this_cluster().block_rank();
+    int par = 0;
     for (;;) {
-        const int q = next_case(a.next, &slot);
+        const int q = cluster_next_case<CL>(a.next, &slot);
         if (q >= a.ncase) break;
         const int cid = a.order[q];
-        const int r0 = a.start[cid], r1 = r0 + a.count[cid];
+        const int n = a.count[cid], chunk = (n + CL - 1) / CL;
+        const int r0 = a.start[cid] + min(n, rank * chunk);
+        const int r1 = a.start[cid] + min(n, (rank + 1) * chunk);
         const int i0 = r0 + threadIdx.x;
         double v6[6] = {0, 0, 0, 0, 0, 0};
         const int all[3] = {1, 1, 1};
@@ -693,7 +699,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                 v6[2 * c + 1] += ri * ri;
             }
         }
-        bsum<BLOCK, RED, 6>(v6, tot);
+        csum<BLOCK, RED, CL, 6>(v6, tot, cpart, par);
         if (threadIdx.x == 0) {
             s_nact = 0;
             for (int c = 0; c < 3; ++c) {
@@ -746,7 +752,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                     a.y[j] = pn * di;
                 }
             }
-            __syncthreads();
+            csync<CL>();      // the product gathers other rows' y
             double v3[3] = {0, 0, 0};
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
@@ -762,7 +768,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                     v3[c] += rh[c] * ay[c];
                 }
             }
-            bsum<BLOCK, RED, 3>(v3, tot);
+            csum<BLOCK, RED, CL, 3>(v3, tot, cpart, par);
             if (threadIdx.x == 0)
                 for (int c = 0; c < 3; ++c) {
                     if (!s_active[c]) continue;
@@ -793,7 +799,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                     a.z[j] = si * di;
                 }
             }
-            __syncthreads();
+            csync<CL>();      // the product gathers other rows' z
             double w6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll U
             for (int i = i0; i < r1; i += BLOCK) {
@@ -811,7 +817,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                     w6[2 * c + 1] += ti * ti;
                 }
             }
-            bsum<BLOCK, RED, 6>(w6, tot);
+            csum<BLOCK, RED, CL, 6>(w6, tot, cpart, par);
             if (threadIdx.x == 0)
                 for (int c = 0; c < 3; ++c)
                     if (s_active[c]) s_omega[c] = tot[2 * c + 1] > 0.0 ? tot[2 * c] / tot[2 * c + 1] : 0.0;
@@ -840,7 +846,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                     u6[2 * c + 1] += rn[c] * rn[c];
                 }
             }
-            bsum<BLOCK, RED, 6>(u6, tot);
+            csum<BLOCK, RED, CL, 6>(u6, tot, cpart, par);
             if (threadIdx.x == 0)
                 for (int c = 0; c < 3; ++c) {
                     if (!s_active[c]) continue;
@@ -856,7 +862,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
                 }
             __syncthreads();
         }
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0 && rank == 0)
             for (int c = 0; c < 3; ++c) {
                 DevSolveStats *st = a.stats + (size_t)cid * kStatStride + c;
                 st->iters = s_iters[c];
@@ -875,12 +881,12 @@ template <int BLOCK, int U, int RED, int CL>
 fv_status launch_batch_solvers(fv_batch *bt, int which, const void *argp)
 {
     const fv_mesh *m = bt->mesh;
-    constexpr int BB = BLOCK < 512 ? BLOCK : 512;      // momentum solve: one block per case
-    const void *fn = which == 0 ? (const void *)k_bicgstab_batch<BB, U, RED>
+    constexpr int BB = BLOCK < 512 ? BLOCK : 512;      // momentum solve: blocks of <= 512
+    const void *fn = which == 0 ? (const void *)k_bicgstab_batch<BB, U, RED, CL>
                    : which == 1 ? (const void *)k_pcg_batch<BLOCK, U, RED, CL>
                                 : (const void *)k_pcg_mixed_batch<BLOCK, U, RED, CL>;
     const int block = which == 0 ? BB : BLOCK;
-    const int cl = which == 0 ? 1 : CL;
+    const int cl = CL;
     int per_sm = 0;
     FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
     if (per_sm < 1) per_sm = 1;
