@@ -664,8 +664,10 @@ __device__ __forceinline__ void bspmv3(const BBi &a, int i, double d, const doub
 
 // A case is owned by a cluster of CL blocks (rows split evenly between them),
 // with the cluster barriers and sums of the pressure solve; CL = 1: one block.
+// Registers are capped so that 1024 threads per SM stay resident (without the
+// cap the compiler took up to 128 per thread: one 512-thread block per SM).
 template <int BLOCK, int U, int RED, int CL>
-__global__ void __launch_bounds__(BLOCK) k_bicgstab_batch(BBi a)
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bicgstab_batch(BBi a)
 {
     __shared__ int slot;
     __shared__ double tot[6], cpart[16];
