@@ -121,6 +121,39 @@ def test_bicgstab_matches_dense_on_momentum_systems(which):
     assert it == 0 and not x.any()
 
 
+def test_bicgstab_stopping_rule_and_warm_start():
+    """The rules both BiCGStab implementations share: stop once the updated
+    residual meets max(tol ||b||, reltol ||r0||) (it equals the true residual
+    b - A x to rounding), status -1 when the iteration limit comes first,
+    no iteration from an exact start, x = 0 for a zero right-hand side."""
+    m = mg.cavity3d(5)
+    om, cs = _stepped_case(m, 0.01, 0.05, 3)
+    d, up, lo, src = cs.momentum_system(True, 0.05)
+    own, nei = om.addressing()
+    A = dense_from_ldu(own, nei, d, up, lo)
+    b = src[0]
+    nb = np.linalg.norm(b)
+    xs = np.linalg.solve(A, b)
+    for tol in (1e-3, 1e-6, 1e-9):
+        x, it, r0, r1, st = O.bicgstab(own, nei, d, up, lo, b, np.zeros(m.n_cells), tol=tol)
+        assert st == 0 and r1 <= tol and it >= 1
+        assert abs(np.linalg.norm(b - A @ x) / nb - r1) <= 1e-6 * r1 + 1e-15
+        # one iteration fewer would not have met the tolerance
+        x2, it2, _, r2, st2 = O.bicgstab(own, nei, d, up, lo, b, np.zeros(m.n_cells), tol=tol,
+                                         maxit=it - 1)
+        assert st2 == -1 and r2 > tol and it2 == it - 1
+    # exact start: zero iterations
+    x, it, r0, r1, st = O.bicgstab(own, nei, d, up, lo, b, xs, tol=1e-8)
+    assert it == 0 and st == 0
+    # zero right-hand side: x = 0, no iterations, whatever the start
+    x, it, r0, r1, st = O.bicgstab(own, nei, d, up, lo, 0 * b, xs, tol=1e-8)
+    assert it == 0 and st == 0 and not x.any()
+    # relative-to-initial tolerance
+    x, it, r0, r1, st = O.bicgstab(own, nei, d, up, lo, b, np.zeros(m.n_cells), tol=0.0,
+                                   reltol=1e-2)
+    assert st == 0 and r1 <= 1e-2 * r0
+
+
 def test_dense_solve_pivoting():
     A = np.array([[0.0, 2.0, 1.0], [1.0, 1.0, 0.0], [3.0, 0.0, 1.0]])
     b = np.array([3.0, 2.0, 4.0])
